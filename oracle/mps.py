@@ -1,0 +1,190 @@
+"""Plain MPS circuit evolution with truncated pivoted-QR splitting (test infrastructure).
+
+ORACLE — slow, obviously correct, complex128.  Only tests, the package smoke
+check and the benchmark's CPU-baseline leg use it; the GPU library never calls
+it.  Every step follows the paper's description:
+
+* State (Sec. II-B.1, Sec. III-A.1): n sites, site i a row-major complex array
+  (chi_i, 2, chi_{i+1}) with chi_0 = chi_n = 1; |0...0> has every site
+  [1, 0] of shape (1, 2, 1).
+* One-qubit gate (Sec. II-A.2, tensor application Sec. III-C.2):
+  A[l, s, r] <- sum_s' u[s, s'] A[l, s', r].
+* Two-qubit gate on (i, i+1) (Sec. III-C.2): contract the two sites over the
+  shared bond (Sec. III-B.1), contract the gate into the physical indices,
+  theta[l, a, b, r] = sum_{cd} g[2a+b, 2c+d] X[l, c, d, r], read theta as the
+  (2 chi_l) x (2 chi_r) matrix with row (l, a) and column (b, r), and split it
+  by the truncated column-pivoted QR theta P = Q R (Sec. III-B.2, QR with
+  pivoting) stopped after k = min(2 chi_l, 2 chi_r, chi_max) pivots:
+  the left site becomes Q[:, :k] reshaped (chi_l, 2, k) and the right site
+  R[:k, :] P^T reshaped (k, 2, chi_r).  The state is never renormalised, so
+  its squared norm is the norm fidelity of Sec. III-E.
+* SWAP (Sec. III-C.4): the two-qubit path with the SWAP gate; a gate on
+  non-adjacent positions lo < hi moves the qubit at lo rightwards by SWAPs on
+  bonds (lo, lo+1) ... (hi-2, hi-1), applies the gate on (hi-1, hi), then
+  SWAPs back in reverse order.
+* Orthogonality centre (Sec. III-C.1): under the "canon" policy the centre is
+  moved to site i before a gate on (i, i+1) by plain QR (rightward move: the Q
+  factor stays, R is multiplied into the next site) or LQ (leftward move, as QR
+  of the conjugate transpose; L is multiplied into the previous site), without
+  truncation; after the gate the centre is site i+1.  The "local" policy never
+  moves the centre.
+* Amplitude: <x|psi> = A_0[:, x_0, :] A_1[:, x_1, :] ... (1x1 product).
+* Norm fidelity (Sec. III-E): F = <psi|psi> by transfer matrices
+  E <- sum_s A[:, s, :]^H E A[:, s, :].
+"""
+
+import numpy as np
+
+from . import qr as _qr
+
+
+def _swap_gate():
+    g = np.zeros((4, 4), dtype=np.complex128)
+    for a in range(2):
+        for b in range(2):
+            g[2 * b + a, 2 * a + b] = 1.0
+    return g
+
+
+SWAP = _swap_gate()
+
+
+class OracleMPS:
+    def __init__(self, n, chi_max, policy="canon"):
+        assert n >= 1 and chi_max >= 1 and policy in ("canon", "local")
+        self.n = n
+        self.chi_max = chi_max
+        self.policy = policy
+        self.sites = []
+        for _ in range(n):
+            s = np.zeros((1, 2, 1), dtype=np.complex128)
+            s[0, 0, 0] = 1.0
+            self.sites.append(s)
+        self.centre = 0
+        self.discarded = []  # discarded weight of every two-qubit split, in order
+        self.n_two_site = 0
+
+    # ---- state access -------------------------------------------------
+    def bond_dims(self):
+        return [1] + [s.shape[2] for s in self.sites]
+
+    def set_sites(self, sites, centre=0):
+        assert len(sites) == self.n
+        for i in range(self.n - 1):
+            assert sites[i].shape[2] == sites[i + 1].shape[0]
+        self.sites = [np.array(s, dtype=np.complex128, copy=True) for s in sites]
+        self.centre = centre
+
+    def copy(self):
+        o = OracleMPS(self.n, self.chi_max, self.policy)
+        o.sites = [s.copy() for s in self.sites]
+        o.centre = self.centre
+        o.discarded = list(self.discarded)
+        o.n_two_site = self.n_two_site
+        return o
+
+    # ---- gates -------------------------------------------------------
+    def apply_1q(self, q, u):
+        u = np.asarray(u, dtype=np.complex128)
+        self.sites[q] = np.einsum("ab,lbr->lar", u, self.sites[q])
+
+    def _move_right(self, j):
+        a = self.sites[j]
+        cl, _, cr = a.shape
+        q, r, _, _ = _qr.cpqr(a.reshape(2 * cl, cr), pivot=False)
+        k = q.shape[1]
+        self.sites[j] = np.ascontiguousarray(q).reshape(cl, 2, k)
+        nxt = self.sites[j + 1]
+        self.sites[j + 1] = (r @ nxt.reshape(cr, -1)).reshape(k, 2, nxt.shape[2])
+
+    def _move_left(self, j):
+        a = self.sites[j]
+        cl, _, cr = a.shape
+        m = a.reshape(cl, 2 * cr)
+        q, r, _, _ = _qr.cpqr(m.conj().T, pivot=False)  # m^H = q r  ->  m = r^H q^H
+        k = q.shape[1]
+        self.sites[j] = np.ascontiguousarray(q.conj().T).reshape(k, 2, cr)
+        prv = self.sites[j - 1]
+        self.sites[j - 1] = (prv.reshape(-1, cl) @ r.conj().T).reshape(prv.shape[0], 2, k)
+
+    def move_centre(self, target):
+        while self.centre < target:
+            self._move_right(self.centre)
+            self.centre += 1
+        while self.centre > target:
+            self._move_left(self.centre)
+            self.centre -= 1
+
+    def apply_2q(self, i, g, chi_max=None):
+        """Gate g on adjacent sites (i, i+1); returns the discarded weight."""
+        chi = self.chi_max if chi_max is None else min(chi_max, self.chi_max)
+        if self.policy == "canon":
+            self.move_centre(i)
+        g = np.asarray(g, dtype=np.complex128).reshape(2, 2, 2, 2)
+        a, b = self.sites[i], self.sites[i + 1]
+        cl, cm, cr = a.shape[0], a.shape[2], b.shape[2]
+        x = (a.reshape(2 * cl, cm) @ b.reshape(cm, 2 * cr)).reshape(cl, 2, 2, cr)
+        theta = np.einsum("abcd,lcdr->labr", g, x).reshape(2 * cl, 2 * cr)
+        q, r, jpvt, disc = _qr.cpqr(theta, kmax=chi, pivot=True)
+        k = q.shape[1]
+        right = np.zeros((k, 2 * cr), dtype=np.complex128)
+        right[:, jpvt] = r
+        self.sites[i] = np.ascontiguousarray(q).reshape(cl, 2, k)
+        self.sites[i + 1] = right.reshape(k, 2, cr)
+        if self.policy == "canon":
+            self.centre = i + 1
+        self.discarded.append(disc)
+        self.n_two_site += 1
+        return disc
+
+    def swap(self, i, chi_max=None):
+        return self.apply_2q(i, SWAP, chi_max)
+
+    def apply_2q_routed(self, q1, q2, g, chi_max=None):
+        """Gate g on the ordered pair (q1, q2), routed by SWAP chains if needed."""
+        g = np.asarray(g, dtype=np.complex128)
+        assert q1 != q2
+        if q1 > q2:
+            q1, q2 = q2, q1
+            g = SWAP @ g @ SWAP
+        for b in range(q1, q2 - 1):
+            self.swap(b, chi_max)
+        self.apply_2q(q2 - 1, g, chi_max)
+        for b in range(q2 - 2, q1 - 1, -1):
+            self.swap(b, chi_max)
+
+    def run(self, ops, chi_max=None):
+        for op in ops:
+            if op[0] == "1q":
+                self.apply_1q(op[1], op[2])
+            else:
+                self.apply_2q_routed(op[1], op[2], op[3], chi_max)
+
+    # ---- observables -------------------------------------------------
+    def amplitude(self, bits):
+        v = np.ones((1, 1), dtype=np.complex128)
+        for i in range(self.n):
+            v = v @ self.sites[i][:, int(bits[i]), :]
+        return complex(v[0, 0])
+
+    def overlap(self, other):
+        """<self|other> by transfer matrices."""
+        e = np.ones((1, 1), dtype=np.complex128)
+        for a, b in zip(self.sites, other.sites):
+            e = sum(a[:, s, :].conj().T @ e @ b[:, s, :] for s in range(2))
+        return complex(e[0, 0])
+
+    def norm2(self):
+        """Norm fidelity <psi|psi> (Sec. III-E)."""
+        return self.overlap(self).real
+
+    def centre_norm2(self):
+        return float(np.vdot(self.sites[self.centre], self.sites[self.centre]).real)
+
+    def statevector(self):
+        """Dense 2^n vector (small n only); index bit n-1-i is site i."""
+        v = self.sites[0].reshape(2, -1)
+        for i in range(1, self.n):
+            s = self.sites[i]
+            v = (v @ s.reshape(s.shape[0], -1)).reshape(-1, s.shape[2])
+        return v.reshape(-1)

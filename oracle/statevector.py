@@ -1,0 +1,44 @@
+"""Brute-force statevector evolution (the oracle's own check, n <= ~16).
+
+ORACLE — test infrastructure.  The state is the 2^n vector of Sec. II-A.1 with
+qubit 0 as the most significant bit of the index; gates act as in Sec. II-A.2.
+No truncation, no MPS: the exact state a circuit produces.
+"""
+
+import numpy as np
+
+
+def zero_state(n):
+    v = np.zeros(2**n, dtype=np.complex128)
+    v[0] = 1.0
+    return v
+
+
+def apply_1q(v, n, q, u):
+    t = v.reshape(2**q, 2, 2 ** (n - q - 1))
+    return np.einsum("ab,xby->xay", np.asarray(u), t).reshape(-1)
+
+
+def apply_2q(v, n, q1, q2, g):
+    """Gate g (row 2a+b, col 2c+d) with a on qubit q1 and b on qubit q2."""
+    t = v.reshape([2] * n)
+    g4 = np.asarray(g).reshape(2, 2, 2, 2)
+    t = np.tensordot(g4, t, axes=([2, 3], [q1, q2]))  # axes: a, b, rest...
+    rest = [i for i in range(n) if i not in (q1, q2)]
+    order = [0] * n
+    order[q1] = 0
+    order[q2] = 1
+    for pos, ax in enumerate(rest):
+        order[ax] = pos + 2
+    return np.transpose(t, order).reshape(-1)
+
+
+def run(ops, n, v=None):
+    if v is None:
+        v = zero_state(n)
+    for op in ops:
+        if op[0] == "1q":
+            v = apply_1q(v, n, op[1], op[2])
+        else:
+            v = apply_2q(v, n, op[1], op[2], op[3])
+    return v

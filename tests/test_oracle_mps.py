@@ -1,0 +1,229 @@
+"""Pins of the oracle's MPS evolution (CPU only).
+
+Checked against the brute-force statevector (no truncation), closed forms
+(Bell/GHZ, QFT of a basis state, phase estimation), the paper's printed gates
+and state examples (tests/golden), and the truncation identities of the
+norm fidelity (Sec. III-E).
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mps as omps
+from oracle import statevector as sv
+from workloads import circuits, gates, states
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def cmat(rows):
+    return np.array([[complex(re, im) for re, im in row] for row in rows])
+
+
+def test_gate_fixtures_match_paper():
+    g = load("paper_gates.json")
+    s = 1 / np.sqrt(2)
+    for name, fn in [("hadamard", gates.hadamard), ("sqrt_x", gates.sqrt_x),
+                     ("sqrt_y", gates.sqrt_y), ("sqrt_w", gates.sqrt_w), ("fsim", gates.fsim)]:
+        m = cmat(g[name]["m"]) * (s if g[name]["scale"] == "s" else 1.0)
+        assert np.abs(fn() - m).max() < 1e-15, name
+        assert np.abs(fn().conj().T @ fn() - np.eye(len(m))).max() < 1e-14
+    assert np.abs(gates.r_k(2) - cmat(g["r_k"]["k2"])).max() < 1e-15
+    assert np.abs(gates.r_k(3) - cmat(g["r_k"]["k3"])).max() < 1e-15
+
+
+def test_bell_state_golden():
+    b = load("bell_state.json")
+    m = omps.OracleMPS(2, 4)
+    m.run(circuits.ghz(2))
+    ref = np.array([complex(*x) for x in b["amplitudes"]])
+    assert np.abs(m.statevector() - ref).max() < 1e-15
+
+
+def test_tensor_product_order_golden():
+    p = load("tensor_product_order.json")
+    a1, b1 = [complex(*x) for x in p["psi1"]]
+    a2, b2 = [complex(*x) for x in p["psi2"]]
+
+    def prep(a, b):  # unitary with first column (a, b)
+        return np.array([[a, -np.conj(b)], [b, np.conj(a)]])
+
+    m = omps.OracleMPS(2, 4)
+    m.apply_1q(0, prep(a1, b1))
+    m.apply_1q(1, prep(a2, b2))
+    want = {"a1a2": a1 * a2, "a1b2": a1 * b2, "b1a2": b1 * a2, "b1b2": b1 * b2}
+    for idx, key in enumerate(p["order"]):
+        bits = [(idx >> 1) & 1, idx & 1]
+        assert m.amplitude(bits) == pytest.approx(want[key], abs=1e-15)
+
+
+@pytest.mark.parametrize("policy", ["canon", "local"])
+def test_brickwall_exact_vs_statevector(policy):
+    """12-qubit depth-8 Haar brick-wall, chi_max = 64: no truncation, F = 1."""
+    n, depth = 12, 8
+    ops = circuits.brickwall(n, depth, seed=1)
+    m = omps.OracleMPS(n, 64, policy)
+    m.run(ops)
+    v = sv.run(ops, n)
+    assert np.abs(m.statevector() - v).max() < 1e-12
+    assert m.norm2() == pytest.approx(1.0, abs=1e-12)
+    assert max(m.bond_dims()) == 64
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        bits = rng.integers(0, 2, n)
+        idx = int("".join(map(str, bits)), 2)
+        assert abs(m.amplitude(bits) - v[idx]) < 1e-12
+    assert max(m.discarded) < 1e-24
+
+
+@pytest.mark.parametrize("n", [2, 5, 9])
+def test_ghz_closed_form(n):
+    m = omps.OracleMPS(n, 8)
+    m.run(circuits.ghz(n))
+    s = 1 / np.sqrt(2)
+    assert m.amplitude([0] * n) == pytest.approx(s, abs=1e-14)
+    assert m.amplitude([1] * n) == pytest.approx(s, abs=1e-14)
+    v = m.statevector()
+    v[0] -= s
+    v[-1] -= s
+    assert np.abs(v).max() < 1e-14
+
+
+@pytest.mark.parametrize("x", [0, 5, 37])
+def test_qft_of_basis_state_closed_form(x):
+    """QFT (swaps omitted) of |x>: amplitude of |y> is 2^{-t/2} exp(2 pi i x rev(y) / 2^t),
+    rev(y) = sum_j y_j 2^j with y_j the bit on position j."""
+    t = 7
+    ops = circuits.basis_state(t, x) + circuits.qft_noswap(list(range(t)))
+    m = omps.OracleMPS(t, 64)
+    m.run(ops)
+    v = m.statevector()
+    for y in range(2**t):
+        bits = [(y >> (t - 1 - j)) & 1 for j in range(t)]
+        rev = sum(b << j for j, b in enumerate(bits))
+        want = 2 ** (-t / 2) * np.exp(2j * np.pi * x * rev / 2**t)
+        assert abs(v[y] - want) < 1e-13
+
+
+def test_iqft_inverts_qft():
+    t = 6
+    rng = np.random.default_rng(4)
+    ops = circuits.brickwall(t, 3, seed=9)
+    ref = sv.run(ops, t)
+    m = omps.OracleMPS(t, 64)
+    m.run(ops + circuits.qft_noswap(list(range(t))) + circuits.iqft_noswap(list(range(t))))
+    assert np.abs(m.statevector() - ref).max() < 1e-12
+    del rng
+
+
+def test_qpe_dyadic_exact():
+    ops, y = circuits.qpe_dyadic(6, 3, seed=2)
+    m = omps.OracleMPS(9, 64)
+    m.run(ops)
+    v = m.statevector().reshape(2**6, 2**3)
+    prob = np.sum(np.abs(v) ** 2, axis=1)
+    assert prob[y] == pytest.approx(1.0, abs=1e-12)
+
+
+def test_qpe_fejer_kernel():
+    tc, tt = 6, 3
+    ops, phi = circuits.qpe(tc, tt, seed=5)
+    m = omps.OracleMPS(tc + tt, 64)
+    m.run(ops)
+    v = m.statevector().reshape(2**tc, 2**tt)
+    prob = np.sum(np.abs(v) ** 2, axis=1)
+    xs = np.arange(2**tc)
+    for y in range(2**tc):
+        amp = np.sum(np.exp(2j * np.pi * xs * (phi - y / 2**tc))) / 2**tc
+        assert prob[y] == pytest.approx(abs(amp) ** 2, abs=1e-12)
+
+
+def test_routing_vs_statevector():
+    """3x3 grid circuit with vertical couplers routed by SWAP chains, no truncation."""
+    ops = circuits.grid_rcs(3, 3, 4, seed=3)
+    m = omps.OracleMPS(9, 32)
+    m.run(ops)
+    v = sv.run(ops, 9)
+    assert np.abs(m.statevector() - v).max() < 1e-12
+
+
+def test_routing_far_pair_both_orders():
+    rng = np.random.default_rng(8)
+    g = gates.haar_unitary(rng, 4)
+    base = circuits.brickwall(6, 2, seed=4)
+    for q1, q2 in [(0, 5), (5, 1), (2, 4)]:
+        ops = base + [("2q", q1, q2, g)]
+        m = omps.OracleMPS(6, 16)
+        m.run(ops)
+        assert np.abs(m.statevector() - sv.run(ops, 6)).max() < 1e-12
+
+
+def test_truncation_identity_canon():
+    """Under the canonical policy every split removes exactly its discarded weight
+    from the norm fidelity: F_after = F_before - delta (Sec. III-E)."""
+    n = 10
+    ops = circuits.brickwall(n, 10, seed=6)
+    m = omps.OracleMPS(n, 6, "canon")
+    f = 1.0
+    for op in ops:
+        if op[0] == "1q":
+            m.apply_1q(op[1], op[2])
+            continue
+        d = m.apply_2q(op[1], op[3])
+        f_new = m.norm2()
+        assert f_new == pytest.approx(f - d, rel=1e-11, abs=1e-14)
+        assert m.centre_norm2() == pytest.approx(f_new, rel=1e-11)
+        f = f_new
+    assert f < 1.0 and sum(m.discarded) > 0
+    assert f == pytest.approx(1.0 - sum(m.discarded), rel=1e-10)
+
+
+def test_canonical_form_after_moves():
+    n = 8
+    m = omps.OracleMPS(n, 16, "canon")
+    m.run(circuits.brickwall(n, 6, seed=2))
+    m.move_centre(3)
+    for i, s in enumerate(m.sites):
+        cl, _, cr = s.shape
+        if i < 3:
+            a = s.reshape(2 * cl, cr)
+            assert np.abs(a.conj().T @ a - np.eye(cr)).max() < 1e-12
+        elif i > 3:
+            a = s.reshape(cl, 2 * cr)
+            assert np.abs(a @ a.conj().T - np.eye(cl)).max() < 1e-12
+
+
+def test_norm_fidelity_tracks_overlap_fidelity():
+    """Sec. III-E (Fig. 5): the norm fidelity approximates the overlap fidelity with
+    the exact state, and pivoted QR tends to underestimate it.  The overlap is
+    taken with the truncated state normalised, |<E|T>|^2 / <T|T>."""
+    n = 12
+    ops = circuits.brickwall(n, 12, seed=10)
+    exact = sv.run(ops, n)
+    for chi in (16, 24, 32):
+        m = omps.OracleMPS(n, chi, "canon")
+        m.run(ops)
+        fbar = m.norm2()
+        t = m.statevector()
+        fov = abs(np.vdot(exact, t)) ** 2 / fbar
+        assert 0 < fbar < 1 and 0 < fov < 1
+        assert abs(fbar - fov) < 0.05 * fov
+        assert fbar <= fov
+
+
+def test_random_canonical_state_has_unit_norm():
+    n = 10
+    bonds = states.max_bond_dims(n, 8)
+    sites = states.random_canonical_mps(n, bonds, 4, seed=1)
+    m = omps.OracleMPS(n, 8)
+    m.set_sites(sites, centre=4)
+    assert m.norm2() == pytest.approx(1.0, abs=1e-12)
+    assert m.centre_norm2() == pytest.approx(1.0, abs=1e-12)
