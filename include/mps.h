@@ -1,0 +1,240 @@
+/*
+ * mps.h — C ABI of the GB300 matrix-product-state two-site gate engine.
+ *
+ * The engine evolves a matrix product state (MPS) of n qubits under one- and
+ * two-qubit gates (Sec. II-B.1 MPS definition; Sec. III-C tensor application
+ * and site permutation).  A two-qubit gate on neighbouring sites (i, i+1):
+ *
+ *   1. contracts A_i (chi_l x 2 x chi_m) and A_{i+1} (chi_m x 2 x chi_r) over
+ *      their shared bond (Sec. III-B.1 bond contraction) and the 4x4 gate into
+ *      the physical indices, giving theta as a (2 chi_l) x (2 chi_r) matrix
+ *      with row (l, a) and column (b, r);
+ *   2. splits theta by a column-pivoted Householder QR, theta P = Q R
+ *      (Sec. III-B.2, Table of decomposition routines: QR with pivoting),
+ *      stopped after k = min(2 chi_l, 2 chi_r, chi_max) pivots;
+ *   3. stores Q[:, :k] as the new A_i (chi_l x 2 x k) and R[:k, :] P^T as the
+ *      new A_{i+1} (k x 2 x chi_r).  The state is not renormalised: its squared
+ *      norm is the norm fidelity F = <psi|psi> of Sec. III-E.
+ *
+ * Conventions
+ *   - Site layout: row-major (chi_l, 2, chi_r), the flat row-major layout of
+ *     Sec. III-A.1.  Site 0 holds the most significant bit of a basis index
+ *     (tensor-product order of Sec. II-A.1).  chi_0 = chi_n = 1.
+ *   - One-qubit gate u[out*2 + in].  Two-qubit gate g[(2a+b)*4 + (2c+d)],
+ *     row = output; a/c label the first listed qubit, b/d the second.
+ *   - Bond dimensions grow structurally: a split always keeps
+ *     k = min(2 chi_l, 2 chi_r, chi_max) columns, with no rank tolerance.
+ *   - Policies: MPS_POLICY_CANON keeps one orthogonality centre and moves it to
+ *     site i (QR rightward / LQ leftward, no truncation; Sec. III-C.1) before a
+ *     gate on (i, i+1); afterwards the centre is i+1.  MPS_POLICY_LOCAL never
+ *     moves the centre (each split truncates its own theta).
+ *   - Precisions: MPS_PREC_FP64 stores complex128 and computes in FP64.
+ *     MPS_PREC_MIXED stores complex64, runs the contractions and the QR bulk in
+ *     FP32-class arithmetic, and keeps column norms, reflector norms/beta/tau
+ *     and pivot comparisons in FP64.
+ *
+ * Ownership and errors
+ *   - Host arrays passed in are read before the call returns; host arrays
+ *     passed out are written before it returns.  The library owns all device
+ *     memory of a handle (allocated at create, sized for the largest bond
+ *     dims the chain and chi_max allow), except in the raw-pointer calls
+ *     (mps_two_site_*), where the caller owns every buffer.
+ *   - Every call returns MPS_OK (0) or a negative MPS_E_* code.  Mutating calls
+ *     are asynchronous on the handle's stream; device-side failures (a bounded
+ *     wait that expired, a failed index check) surface at the next synchronous
+ *     call (mps_sync, mps_amplitude, mps_fidelity_estimate, mps_overlap,
+ *     mps_get_site, mps_discarded_weight).  After such a failure the handle
+ *     rejects further mutation with MPS_E_STATE; mps_last_error() describes it.
+ *   - A handle is not thread-safe; distinct handles may be used from distinct
+ *     threads.
+ */
+#ifndef MPS_GB300_H
+#define MPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPS_OK 0
+#define MPS_E_ARG (-1)         /* invalid argument (checked on the host, nothing launched) */
+#define MPS_E_NOMEM (-2)       /* a device or pinned-host allocation failed */
+#define MPS_E_CUDA (-3)        /* a CUDA runtime call failed (message in mps_last_error) */
+#define MPS_E_TIMEOUT (-4)     /* a bounded device-side wait expired */
+#define MPS_E_STATE (-5)       /* handle is in an error state, or call invalid in this state */
+#define MPS_E_UNSUPPORTED (-6) /* request outside what this build supports */
+
+#define MPS_PREC_FP64 0
+#define MPS_PREC_MIXED 1
+
+#define MPS_POLICY_CANON 0
+#define MPS_POLICY_LOCAL 1
+
+/* host element formats for mps_get_site / mps_set_site */
+#define MPS_HOST_C128 0
+#define MPS_HOST_C64 1
+
+/* mps_config.flags */
+#define MPS_FLAG_PROFILE 1 /* time the tracked kernels with CUDA events (mps_kernel_stats) */
+
+typedef struct mps_s* mps_t;
+typedef struct {
+  double re, im;
+} mps_c128;
+typedef struct {
+  float re, im;
+} mps_c64;
+
+typedef void* (*mps_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*mps_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+  int precision;          /* MPS_PREC_FP64 (default) or MPS_PREC_MIXED */
+  int policy;             /* MPS_POLICY_CANON (default) or MPS_POLICY_LOCAL */
+  int device;             /* CUDA device ordinal; default 0 */
+  void* stream;           /* cudaStream_t to run on; NULL = the library creates one */
+  int panel_width;        /* QR panel width nb in [1, 64]; 0 = default (32) */
+  double wait_timeout_s;  /* limit of every device-side wait; 0 = default (10 s) */
+  mps_alloc_fn alloc;     /* optional device allocator; NULL = cudaMalloc */
+  mps_free_fn free;       /* must be given together with alloc */
+  void* alloc_ctx;        /* passed to alloc/free */
+  int flags;              /* MPS_FLAG_* */
+  int debug_barrier_extra; /* testing only, normally 0: a grid barrier waits for this many
+                              arrivals that never come, so every bounded wait expires and
+                              the call fails with MPS_E_TIMEOUT instead of hanging */
+  int reserved[7];
+} mps_config;
+
+/* Fill *cfg with the defaults listed above. */
+void mps_config_init(mps_config* cfg);
+
+/* Create the state |0...0> of n qubits (every site [1,0], all bonds 1;
+ * Sec. II-B.1), FP64 path, canonical policy, centre at site 0.
+ * n >= 1, chi_max >= 1.  Device memory for every site is reserved up front
+ * for bond dims min(2^b, 2^(n-b), chi_max). */
+int mps_create(mps_t* out, int n, int chi_max);
+/* As mps_create with an explicit configuration (NULL = defaults). */
+int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg);
+/* Release the handle and all its device memory.  NULL is accepted. */
+int mps_destroy(mps_t h);
+
+/* One-qubit gate on `site` (Sec. II-A.2): A[l,s,r] <- sum_s' u[s*2+s'] A[l,s',r]. */
+int mps_apply_1q(mps_t h, int site, const mps_c128 u[4]);
+
+/* Two-qubit gate g on (site, site+1), split by truncated pivoted QR as in the
+ * header comment (Sec. III-C.2, III-B.2).  chi_max (<= the handle's) caps the
+ * new bond; chi_max <= 0 means the handle's value. */
+int mps_apply_2q(mps_t h, int site, const mps_c128 g[16], int chi_max);
+
+/* SWAP of the qubits on (site, site+1): the two-site path with the SWAP gate,
+ * theta[l,a,b,r] = X[l,b,a,r] (Sec. III-C.4 site permutation). */
+int mps_swap(mps_t h, int site, int chi_max);
+
+/* Two-qubit gate on the ordered pair of positions (q1, q2), not necessarily
+ * adjacent (Sec. III-C.4, Sec. III-D.2 SWAP approach).  With lo < hi the
+ * qubit at lo is moved right by SWAPs on bonds (lo,lo+1) .. (hi-2,hi-1), the
+ * gate is applied on (hi-1, hi), and the SWAPs are undone in reverse order. */
+int mps_apply_2q_routed(mps_t h, int q1, int q2, const mps_c128 g[16], int chi_max);
+
+/* All two-qubit gates of one circuit layer, on pairwise disjoint bonds
+ * sites[j], sites[j]+1 (gates[16*j .. 16*j+15]).  Requires
+ * MPS_POLICY_LOCAL (no centre moves, so the gates commute exactly and the
+ * result equals applying them one by one). */
+int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count, int chi_max);
+
+/* <bits|psi> = A_0[:, b_0, :] A_1[:, b_1, :] ... (bits[i] in {0,1} for site i).
+ * Synchronous. */
+int mps_amplitude(mps_t h, const uint8_t* bits, mps_c128* out);
+
+/* Norm fidelity F = <psi|psi> (Sec. III-E).  Canonical policy: the squared
+ * norm of the centre site; local policy: full transfer-matrix contraction.
+ * Synchronous; accumulated in FP64 for both precisions. */
+int mps_fidelity_estimate(mps_t h, double* out);
+
+/* <a|b> by transfer-matrix contraction in FP64 (both handles must have the
+ * same n; precisions may differ).  Synchronous. */
+int mps_overlap(mps_t a, mps_t b, mps_c128* out);
+
+/* Copy the n+1 bond dimensions into out[0..n]. */
+int mps_bond_dims(mps_t h, int* out);
+
+/* Copy site `site` (chi_l*2*chi_r elements, row-major) to host memory in
+ * format host_fmt (MPS_HOST_C128 / MPS_HOST_C64).  cap_elems = capacity of
+ * `host` in elements; MPS_E_ARG if too small.  Synchronous. */
+int mps_get_site(mps_t h, int site, int host_fmt, void* host, size_t cap_elems);
+
+/* Overwrite site `site` with a host array of shape (chi_l, 2, chi_r).  The
+ * bond dims must agree with the neighbours once all sites of a change are set;
+ * mps_set_site itself only checks chi_l/chi_r against the reserved capacity.
+ * Stream-ordered: `host` is read before return (pinned or pageable). */
+int mps_set_site(mps_t h, int site, int chi_l, int chi_r, int host_fmt, const void* host);
+
+/* Declare that the state is in mixed-canonical form with centre `centre`
+ * (caller's guarantee, e.g. after loading sites).  No data is touched. */
+int mps_set_centre(mps_t h, int centre);
+int mps_get_centre(mps_t h, int* out);
+/* Move the orthogonality centre to `target` (QR / LQ without truncation,
+ * Sec. III-C.1). */
+int mps_move_centre(mps_t h, int target);
+
+/* Sum and count of the discarded weights ||theta_trailing||_F^2 of all
+ * two-site splits so far.  Synchronous. */
+int mps_discarded_weight(mps_t h, double* total, long long* count);
+
+/* Use `stream` (a cudaStream_t) for all further work; NULL = the handle's own. */
+int mps_set_stream(mps_t h, void* stream);
+/* Wait for all queued work; surfaces device-side errors. */
+int mps_sync(mps_t h);
+/* Last error message of the handle ("" if none).  Valid until the next call. */
+const char* mps_last_error(mps_t h);
+
+/* Kernel classes tracked by mps_kernel_stats. */
+#define MPS_KCLASS_THETA 0  /* theta contraction + gate epilogue */
+#define MPS_KCLASS_PANEL 1  /* pivoted-QR panel (per-step GEMV, pivots, reflectors) */
+#define MPS_KCLASS_UPDATE 2 /* trailing / block-reflector GEMM updates */
+#define MPS_KCLASS_NORMS 3  /* column-norm recompute */
+#define MPS_KCLASS_FORMQ 4  /* Q formation */
+#define MPS_KCLASS_SPLIT 5  /* site split / reshape / un-pivot */
+#define MPS_KCLASS_OTHER 6  /* 1q gates, centre moves' glue, conversions */
+#define MPS_KCLASS_COUNT 7
+
+typedef struct {
+  long long launches;   /* kernel launches of this class since the last reset */
+  double ms;            /* summed CUDA-event time (only with MPS_FLAG_PROFILE) */
+  double alg_bytes;     /* algorithmic HBM bytes of those launches */
+  double alg_flops;     /* algorithmic real flops of those launches */
+} mps_kstat;
+
+/* Per-class launch counts (always) and event timings (MPS_FLAG_PROFILE).
+ * out must hold MPS_KCLASS_COUNT entries.  Synchronous. */
+int mps_kernel_stats(mps_t h, mps_kstat* out);
+int mps_kernel_stats_reset(mps_t h);
+
+/* ---------------------------------------------------------------------------
+ * Raw-pointer two-site call (no handle).  The caller owns every buffer.
+ *
+ * Applies gate g to the two sites A (chi_l x 2 x chi_m) and B (chi_m x 2 x
+ * chi_r), device arrays in the precision's element type (complex128 for
+ * MPS_PREC_FP64, complex64 for MPS_PREC_MIXED), row-major, and writes
+ * A_out (chi_l x 2 x k) and B_out (k x 2 x chi_r), k = min(2chi_l, 2chi_r,
+ * chi_max) (Sec. III-C.2 with the split of Sec. III-B.2).  A_out may alias A
+ * and B_out may alias B.  *discarded_dev (device double) receives the
+ * discarded weight.  `workspace` must hold mps_two_site_workspace() bytes,
+ * 256-byte aligned.  Asynchronous on `stream` (cudaStream_t, NULL = default). */
+int mps_two_site_workspace(int precision, int chi_l, int chi_m, int chi_r, int chi_max,
+                           size_t* bytes);
+int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_max,
+                       const void* A, const void* B, const mps_c128 g[16], void* A_out,
+                       void* B_out, double* discarded_dev, void* workspace, size_t ws_bytes,
+                       void* stream);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int mps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPS_GB300_H */

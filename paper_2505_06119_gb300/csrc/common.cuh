@@ -1,0 +1,162 @@
+// Shared device/host definitions of the GB300 MPS library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mps.h"
+
+namespace mpsg {
+
+// ---------------------------------------------------------------------------
+// complex element types: c64 = cplx<float>, c128 = cplx<double>
+template <typename R>
+struct __align__(sizeof(R) * 2) cplx {
+  R re, im;
+};
+using c64 = cplx<float>;
+using c128 = cplx<double>;
+
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> mk(R re, R im) {
+  cplx<R> c;
+  c.re = re;
+  c.im = im;
+  return c;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator+(cplx<R> a, cplx<R> b) {
+  return mk<R>(a.re + b.re, a.im + b.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator-(cplx<R> a, cplx<R> b) {
+  return mk<R>(a.re - b.re, a.im - b.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator*(cplx<R> a, cplx<R> b) {
+  return mk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> cconj(cplx<R> a) {
+  return mk<R>(a.re, -a.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ R cabs2(cplx<R> a) {
+  return a.re * a.re + a.im * a.im;
+}
+// acc += a * b
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R>
+__host__ __device__ __forceinline__ void cfma_conj(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename RO, typename RI>
+__host__ __device__ __forceinline__ cplx<RO> ccast(cplx<RI> a) {
+  return mk<RO>((RO)a.re, (RO)a.im);
+}
+
+template <typename T>
+struct real_of;
+template <>
+struct real_of<c64> {
+  using type = float;
+};
+template <>
+struct real_of<c128> {
+  using type = double;
+};
+
+// ---------------------------------------------------------------------------
+// device error word values (written by kernels, read by the host)
+enum : int {
+  DEV_OK = 0,
+  DEV_ERR_TIMEOUT = 1,   // a bounded wait gave up
+  DEV_ERR_BOUNDS = 2,    // an index check failed
+  DEV_ERR_NONFINITE = 3  // a NaN/Inf reached a pivot decision
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch of `expected` CTAs.
+//   bar[0] = arrival count (returns to 0 after every barrier),
+//   bar[1] = generation (monotonic).
+// Every wait is bounded: after `timeout_ns` of spinning, or as soon as another
+// CTA has raised *err, the CTA records DEV_ERR_TIMEOUT (first writer wins) and
+// the call returns false.  Callers leave the kernel when it returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, int* err,
+                                             unsigned long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    unsigned gen = ld_acquire_u32(&bar[1]);
+    unsigned arrived = atom_add_acqrel_u32(&bar[0], 1u);
+    if (arrived == expected - 1) {
+      st_relaxed_u32(&bar[0], 0u);
+      st_release_u32(&bar[1], gen + 1);
+    } else {
+      unsigned long long t0 = globaltimer_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(&bar[1]) == gen) {
+        if (ld_relaxed_i32(err) != DEV_OK) {
+          ok = 0;
+          break;
+        }
+        if ((++spins & 63u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
+          atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace mpsg

@@ -1,0 +1,1134 @@
+// MPS state, two-site pipeline and the C ABI (include/mps.h).
+//
+// Device memory of a handle is reserved once at create: every site for the
+// largest bond dims the chain allows, plus one workspace sized for the
+// largest two-site split.  The per-gate pipeline (Sec. III-C.2 with the split
+// of Sec. III-B.2) is fully stream-ordered: bond dims after a split are known
+// on the host (k = min(2 chi_l, 2 chi_r, chi_max)), so no step waits for the
+// device.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mpsg;
+
+namespace {
+
+constexpr int kDefaultNb = 32;
+constexpr int kMaxNb = 64;
+constexpr int kMaxCoop = 1024;
+constexpr int kNormParts = 256;
+constexpr size_t kAlign = 256;
+constexpr int kDiscLog = 1 << 16;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int max_bond(int n, int b, int chi) {
+  // min(2^b, 2^(n-b), chi) without overflow
+  int e = std::min(b, n - b);
+  if (e >= 30) return chi;
+  return std::min(1 << e, chi);
+}
+
+// ---------------------------------------------------------------------------
+// workspace of one two-site split (either precision); carved from one buffer
+struct WsLayout {
+  size_t W, Q, F, vn1, vn2, jpvt, inv, tau, Tfac, Y, Z, red_norm, red_w, red_argv, red_argi, alpha,
+      bar, err, disc, total;
+};
+
+WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int64_t& ldw, int64_t& ldq) {
+  WsLayout L;
+  ldw = (int64_t)std::max(4, (mmax + 3) / 4 * 4);
+  ldq = ldw;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  int npan = (kmax + nb - 1) / nb;
+  int wide = std::max(nmax, kmax);
+  L.W = take(esz * (size_t)ldw * std::max(nmax, 1));
+  L.Q = take(esz * (size_t)ldq * std::max(kmax, 1));
+  L.F = take(esz * (size_t)std::max(nmax, 1) * nb);
+  L.vn1 = take(8 * (size_t)std::max(nmax, 1));
+  L.vn2 = take(8 * (size_t)std::max(nmax, 1));
+  L.jpvt = take(4 * (size_t)std::max(nmax, 1));
+  L.inv = take(4 * (size_t)std::max(nmax, 1));
+  L.tau = take(esz * (size_t)std::max(kmax, 1));
+  L.Tfac = take(esz * (size_t)std::max(npan, 1) * nb * nb);
+  L.Y = take(esz * (size_t)nb * std::max(wide, 1));
+  L.Z = take(esz * (size_t)nb * std::max(wide, 1));
+  L.red_norm = take(8 * (size_t)G);
+  L.red_w = take(16 * (size_t)G * nb);
+  L.red_argv = take(8 * (size_t)G);
+  L.red_argi = take(4 * (size_t)G);
+  L.alpha = take(16);
+  L.bar = take(16);
+  L.err = take(16);
+  L.disc = take(8);
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+struct Ws {
+  T* W;
+  int64_t ldw;
+  T* Q;
+  int64_t ldq;
+  T* F;
+  double* vn1;
+  double* vn2;
+  int* jpvt;
+  int* inv;
+  T* tau;
+  T* Tfac;
+  T* Y;
+  T* Z;
+  double* red_norm;
+  c128* red_w;
+  double* red_argv;
+  int* red_argi;
+  c128* alpha;
+  unsigned* bar;
+  int* err;
+  double* disc;
+};
+
+template <typename T>
+Ws<T> ws_views(char* base, const WsLayout& L, int64_t ldw, int64_t ldq) {
+  Ws<T> w;
+  w.W = (T*)(base + L.W);
+  w.ldw = ldw;
+  w.Q = (T*)(base + L.Q);
+  w.ldq = ldq;
+  w.F = (T*)(base + L.F);
+  w.vn1 = (double*)(base + L.vn1);
+  w.vn2 = (double*)(base + L.vn2);
+  w.jpvt = (int*)(base + L.jpvt);
+  w.inv = (int*)(base + L.inv);
+  w.tau = (T*)(base + L.tau);
+  w.Tfac = (T*)(base + L.Tfac);
+  w.Y = (T*)(base + L.Y);
+  w.Z = (T*)(base + L.Z);
+  w.red_norm = (double*)(base + L.red_norm);
+  w.red_w = (c128*)(base + L.red_w);
+  w.red_argv = (double*)(base + L.red_argv);
+  w.red_argi = (int*)(base + L.red_argi);
+  w.alpha = (c128*)(base + L.alpha);
+  w.bar = (unsigned*)(base + L.bar);
+  w.err = (int*)(base + L.err);
+  w.disc = (double*)(base + L.disc);
+  return w;
+}
+
+struct Knobs {
+  int nb;
+  int G;
+  double flag_tol;
+  unsigned long long timeout_ns;
+  unsigned barrier_extra;
+};
+
+template <typename T>
+QrPlan<T> make_plan(const Ws<T>& w, const Knobs& kn, int m, int n, int k, int pivot, double* disc_slot,
+                    double* disc_total) {
+  QrPlan<T> p;
+  p.m = m;
+  p.n = n;
+  p.k = k;
+  p.nb = kn.nb;
+  p.pivot = pivot;
+  p.W = w.W;
+  p.ldw = w.ldw;
+  p.tau = w.tau;
+  p.jpvt = w.jpvt;
+  p.Tfac = w.Tfac;
+  p.F = w.F;
+  p.vn1 = w.vn1;
+  p.vn2 = w.vn2;
+  p.red_norm = w.red_norm;
+  p.red_w = w.red_w;
+  p.red_argv = w.red_argv;
+  p.red_argi = w.red_argi;
+  p.alpha_slot = w.alpha;
+  p.bar = w.bar;
+  p.err = w.err;
+  p.discarded = disc_slot;
+  p.disc_total = disc_total;
+  p.Y = w.Y;
+  p.Z = w.Z;
+  p.G = kn.G;
+  p.flag_tol = kn.flag_tol;
+  p.timeout_ns = kn.timeout_ns;
+  p.barrier_extra = kn.barrier_extra;
+  return p;
+}
+
+template <typename T>
+void gate_to_T(const mps_c128* g, int count, T* out) {
+  using R = typename real_of<T>::type;
+  for (int i = 0; i < count; ++i) out[i] = mk<R>((R)g[i].re, (R)g[i].im);
+}
+
+#define CKE(x)                               \
+  do {                                       \
+    cudaError_t e_ = (x);                    \
+    if (e_ != cudaSuccess) return e_;        \
+  } while (0)
+
+// The two-site gate pipeline on raw device pointers (Sec. III-C.2):
+// theta contraction + gate -> truncated pivoted QR -> Q formation -> split.
+template <typename T>
+cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, int chi, const T* A, const T* B,
+                          const T* g, T* Aout, T* Bout, double* disc_slot, double* disc_total, cudaStream_t s,
+                          LaunchHooks* hk) {
+  const int m = 2 * cl, n = 2 * cr;
+  const int k = std::min(std::min(m, n), chi);
+  hook_before(hk, MPS_KCLASS_THETA, ((double)m * cm + (double)cm * n + (double)m * n) * sizeof(T),
+              8.0 * m * n * cm + 32.0 * m * n);
+  CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s));
+  hook_after(hk, MPS_KCLASS_THETA, 1);
+  QrPlan<T> p = make_plan<T>(w, kn, m, n, k, 1, disc_slot, disc_total);
+  CKE(qr_factor<T>(p, s, hk));
+  CKE(qr_form_q<T>(p, w.Q, w.ldq, s, hk));
+  hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * ((double)m * k + (double)k * n) * sizeof(T), 0);
+  // left site (row-major m x k) <- Q (column-major m x k)
+  CKE(transpose_copy<T>(w.Q, w.ldq, Aout, k, k, m, 0, s));
+  // right site (row-major k x n) <- R P^T
+  CKE(split_right<T>(w.W, w.ldw, w.jpvt, w.inv, k, n, Bout, s));
+  hook_after(hk, MPS_KCLASS_SPLIT, 3);
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// profiling / launch accounting
+struct PendingEv {
+  int kclass;
+  cudaEvent_t a, b;
+};
+
+struct Profiler {
+  LaunchHooks hooks;
+  bool enabled = false;
+  cudaStream_t stream = nullptr;
+  mps_kstat stat[MPS_KCLASS_COUNT];
+  std::vector<PendingEv> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t cur_a = nullptr;
+  Profiler() {
+    memset(stat, 0, sizeof(stat));
+    hooks.before = &Profiler::before_cb;
+    hooks.after = &Profiler::after_cb;
+    hooks.ctx = this;
+  }
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  static void before_cb(LaunchHooks* h, int kclass, double bytes, double flops) {
+    Profiler* p = (Profiler*)h->ctx;
+    p->stat[kclass].alg_bytes += bytes;
+    p->stat[kclass].alg_flops += flops;
+    if (p->enabled) {
+      p->cur_a = p->get();
+      cudaEventRecord(p->cur_a, p->stream);
+    }
+  }
+  static void after_cb(LaunchHooks* h, int kclass, int nlaunch) {
+    Profiler* p = (Profiler*)h->ctx;
+    p->stat[kclass].launches += nlaunch;
+    if (p->enabled && p->cur_a) {
+      cudaEvent_t b = p->get();
+      cudaEventRecord(b, p->stream);
+      p->pending.push_back({kclass, p->cur_a, b});
+      p->cur_a = nullptr;
+    }
+  }
+  void drain() {
+    for (auto& e : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) stat[e.kclass].ms += ms;
+      pool.push_back(e.a);
+      pool.push_back(e.b);
+    }
+    pending.clear();
+  }
+  void destroy() {
+    drain();
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct mps_s {
+  int n = 0, chi_max = 0, prec = MPS_PREC_FP64, policy = MPS_POLICY_CANON, device = 0;
+  cudaStream_t stream = nullptr, own_stream = nullptr;
+  mps_alloc_fn ualloc = nullptr;
+  mps_free_fn ufree = nullptr;
+  void* actx = nullptr;
+  std::vector<void*> allocs;
+  std::vector<int> bond, capb;  // bond dims, reserved bond dims
+  std::vector<char*> site;
+  int centre = 0;
+  size_t esz = 16;
+  // workspace
+  char* ws = nullptr;
+  WsLayout L;
+  int64_t ldw = 0, ldq = 0;
+  Knobs kn;
+  // FP64 observables scratch
+  double* d_partial = nullptr;
+  double* d_scalar = nullptr;  // [0] norm, [1] total discarded
+  double* d_disclog = nullptr;
+  c128* d_vec = nullptr;  // 2 * chicap + 1
+  int chicap = 1;
+  // transfer-matrix scratch (lazy)
+  c128* d_E = nullptr;
+  size_t E_elems = 0;
+  long long nsplit = 0;
+  // status
+  int status = MPS_OK;
+  std::string msg;
+  Profiler prof;
+};
+
+namespace {
+
+int fail(mps_t h, int code, const std::string& m) {
+  if (h) {
+    h->msg = m;
+    if (code == MPS_E_TIMEOUT || code == MPS_E_CUDA) h->status = code;
+  }
+  return code;
+}
+
+int cuda_fail(mps_t h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? MPS_E_NOMEM : MPS_E_CUDA, m);
+}
+
+#define CUTRY(h, x, where)                         \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+void* dev_alloc(mps_t h, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = kAlign;
+  if (h->ualloc) {
+    p = h->ualloc(bytes, h->actx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->allocs.push_back(p);
+  return p;
+}
+
+void release(mps_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  h->prof.destroy();
+  for (void* p : h->allocs) {
+    if (h->ufree)
+      h->ufree(p, h->actx);
+    else
+      cudaFree(p);
+  }
+  h->allocs.clear();
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  h->own_stream = nullptr;
+}
+
+template <typename T>
+Ws<T> views(mps_t h) {
+  return ws_views<T>(h->ws, h->L, h->ldw, h->ldq);
+}
+
+int check_device_error(mps_t h) {
+  int dev_err = 0;
+  cudaError_t e = cudaMemcpyAsync(&dev_err, views<c64>(h).err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "device sync");
+  if (dev_err == DEV_ERR_TIMEOUT) return fail(h, MPS_E_TIMEOUT, "a bounded device-side wait expired");
+  if (dev_err != DEV_OK) {
+    h->status = MPS_E_CUDA;
+    return fail(h, MPS_E_CUDA, "device-side check failed (code " + std::to_string(dev_err) + ")");
+  }
+  return MPS_OK;
+}
+
+int usable(mps_t h) {
+  if (!h) return MPS_E_ARG;
+  if (h->status != MPS_OK) {
+    h->msg = "handle is in an error state: " + h->msg;
+    return MPS_E_STATE;
+  }
+  if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, MPS_E_CUDA, "cudaSetDevice failed");
+  return MPS_OK;
+}
+
+// ---- centre moves (Sec. III-C.1): plain QR rightward, LQ leftward, no truncation
+template <typename T>
+int move_right(mps_t h, int j) {
+  using R = typename real_of<T>::type;
+  Ws<T> w = views<T>(h);
+  const int cl = h->bond[j], cr = h->bond[j + 1], cn = h->bond[j + 2];
+  const int m = 2 * cl, n = cr, k = std::min(m, n);
+  T* sj = (T*)h->site[j];
+  T* sn = (T*)h->site[j + 1];
+  cudaStream_t s = h->stream;
+  LaunchHooks* hk = &h->prof.hooks;
+  hook_before(hk, MPS_KCLASS_OTHER, 2.0 * m * n * sizeof(T), 0);
+  CUTRY(h, transpose_copy<T>(sj, n, w.W, w.ldw, m, n, 0, s), "move_right copy");
+  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  QrPlan<T> p = make_plan<T>(w, h->kn, m, n, k, 0, nullptr, nullptr);
+  CUTRY(h, qr_factor<T>(p, s, hk), "move_right qr");
+  CUTRY(h, qr_form_q<T>(p, w.Q, w.ldq, s, hk), "move_right form_q");
+  hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * m * k * sizeof(T), 0);
+  CUTRY(h, transpose_copy<T>(w.Q, w.ldq, sj, k, k, m, 0, s), "move_right split");
+  hook_after(hk, MPS_KCLASS_SPLIT, 1);
+  // next site (k x 2cn) = R (k x cr, upper) * site_{j+1} (cr x 2cn); computed transposed into Q
+  GemmDesc<T> d;
+  d.M = 2 * cn;
+  d.N = k;
+  d.K = cr;
+  d.alpha = mk<R>(1, 0);
+  d.beta = mk<R>(0, 0);
+  d.A = sn;
+  d.lda = 2 * cn;
+  d.a_row = 0;
+  d.a_conj = 0;
+  d.a_mask = MASK_NONE;
+  d.B = w.W;
+  d.ldb = w.ldw;
+  d.b_row = 1;
+  d.b_conj = 0;
+  d.b_mask = MASK_UPPER;
+  d.C = w.Q;
+  d.ldc = 2 * cn;
+  hook_before(hk, MPS_KCLASS_OTHER, ((double)2 * cn * cr + (double)k * cr + 2.0 * cn * k) * sizeof(T),
+              8.0 * 2 * cn * k * cr);
+  CUTRY(h, gemm_simt<T>(d, s), "move_right absorb");
+  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  CUTRY(h, cudaMemcpyAsync(sn, w.Q, sizeof(T) * (size_t)k * 2 * cn, cudaMemcpyDeviceToDevice, s), "move_right copy");
+  h->bond[j + 1] = k;
+  return MPS_OK;
+}
+
+template <typename T>
+int move_left(mps_t h, int j) {
+  using R = typename real_of<T>::type;
+  Ws<T> w = views<T>(h);
+  const int cp = h->bond[j - 1], cl = h->bond[j], cr = h->bond[j + 1];
+  const int m = 2 * cr, n = cl, k = std::min(m, n);
+  T* sj = (T*)h->site[j];
+  T* sp = (T*)h->site[j - 1];
+  cudaStream_t s = h->stream;
+  LaunchHooks* hk = &h->prof.hooks;
+  // W (column-major 2cr x cl) = M^H, M = site j as cl x 2cr row-major
+  hook_before(hk, MPS_KCLASS_OTHER, 2.0 * m * n * sizeof(T), 0);
+  CUTRY(h, copy2d<T>(sj, m, w.W, w.ldw, cl, m, 1, s), "move_left copy");
+  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  QrPlan<T> p = make_plan<T>(w, h->kn, m, n, k, 0, nullptr, nullptr);
+  CUTRY(h, qr_factor<T>(p, s, hk), "move_left qr");
+  CUTRY(h, qr_form_q<T>(p, w.Q, w.ldq, s, hk), "move_left form_q");
+  // site j (k x 2cr row-major) = Q^H
+  hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * m * k * sizeof(T), 0);
+  CUTRY(h, copy2d<T>(w.Q, w.ldq, sj, m, k, m, 1, s), "move_left split");
+  hook_after(hk, MPS_KCLASS_SPLIT, 1);
+  // previous site (2cp x k) = site_{j-1} (2cp x cl) * R^H; transposed: conj(R) (k x cl) * site^T
+  GemmDesc<T> d;
+  d.M = k;
+  d.N = 2 * cp;
+  d.K = cl;
+  d.alpha = mk<R>(1, 0);
+  d.beta = mk<R>(0, 0);
+  d.A = w.W;
+  d.lda = w.ldw;
+  d.a_row = 0;
+  d.a_conj = 1;
+  d.a_mask = MASK_UPPER;
+  d.B = sp;
+  d.ldb = cl;
+  d.b_row = 0;
+  d.b_conj = 0;
+  d.b_mask = MASK_NONE;
+  d.C = w.Q;
+  d.ldc = k;
+  hook_before(hk, MPS_KCLASS_OTHER, ((double)2 * cp * cl + (double)k * cl + 2.0 * cp * k) * sizeof(T),
+              8.0 * 2 * cp * k * cl);
+  CUTRY(h, gemm_simt<T>(d, s), "move_left absorb");
+  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  CUTRY(h, cudaMemcpyAsync(sp, w.Q, sizeof(T) * (size_t)k * 2 * cp, cudaMemcpyDeviceToDevice, s), "move_left copy");
+  h->bond[j] = k;
+  return MPS_OK;
+}
+
+template <typename T>
+int move_centre_t(mps_t h, int target) {
+  while (h->centre < target) {
+    int rc = move_right<T>(h, h->centre);
+    if (rc) return rc;
+    h->centre++;
+  }
+  while (h->centre > target) {
+    int rc = move_left<T>(h, h->centre);
+    if (rc) return rc;
+    h->centre--;
+  }
+  return MPS_OK;
+}
+
+template <typename T>
+int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
+  if (h->policy == MPS_POLICY_CANON) {
+    int rc = move_centre_t<T>(h, i);
+    if (rc) return rc;
+  }
+  Ws<T> w = views<T>(h);
+  T gt[16];
+  gate_to_T<T>(g, 16, gt);
+  const int cl = h->bond[i], cm = h->bond[i + 1], cr = h->bond[i + 2];
+  const int k = std::min(std::min(2 * cl, 2 * cr), chi);
+  double* slot = h->d_disclog + (h->nsplit % kDiscLog);
+  cudaError_t e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
+                                   (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream,
+                                   &h->prof.hooks);
+  if (e != cudaSuccess) return cuda_fail(h, e, "apply_2q");
+  h->bond[i + 1] = k;
+  h->nsplit++;
+  if (h->policy == MPS_POLICY_CANON) h->centre = i + 1;
+  return MPS_OK;
+}
+
+template <typename T>
+int apply_1q_t(mps_t h, int q, const mps_c128* u) {
+  T ut[4];
+  gate_to_T<T>(u, 4, ut);
+  LaunchHooks* hk = &h->prof.hooks;
+  hook_before(hk, MPS_KCLASS_OTHER, 2.0 * h->bond[q] * 2 * h->bond[q + 1] * sizeof(T), 0);
+  cudaError_t e = apply_1q<T>((T*)h->site[q], h->bond[q], h->bond[q + 1], ut, h->stream);
+  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "apply_1q");
+  return MPS_OK;
+}
+
+template <typename T>
+int amplitude_t(mps_t h, const uint8_t* bits, mps_c128* out) {
+  c128* v0 = h->d_vec;
+  c128* v1 = h->d_vec + h->chicap + 1;
+  c128 one = mk<double>(1, 0);
+  CUTRY(h, cudaMemcpyAsync(v0, &one, sizeof(c128), cudaMemcpyHostToDevice, h->stream), "amplitude");
+  LaunchHooks* hk = &h->prof.hooks;
+  for (int i = 0; i < h->n; ++i) {
+    const int cl = h->bond[i], cr = h->bond[i + 1];
+    const T* M = (const T*)h->site[i] + (bits[i] ? cr : 0);
+    hook_before(hk, MPS_KCLASS_OTHER, (double)cl * cr * sizeof(T), 8.0 * cl * cr);
+    CUTRY(h, vecmat<T>(v0, M, 2 * cr, cl, cr, v1, h->stream), "amplitude vecmat");
+    hook_after(hk, MPS_KCLASS_OTHER, 1);
+    std::swap(v0, v1);
+  }
+  c128 r;
+  CUTRY(h, cudaMemcpyAsync(&r, v0, sizeof(c128), cudaMemcpyDeviceToHost, h->stream), "amplitude");
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  out->re = r.re;
+  out->im = r.im;
+  return MPS_OK;
+}
+
+template <typename T>
+int centre_norm_t(mps_t h, double* out) {
+  const int c = h->centre;
+  int64_t cnt = (int64_t)h->bond[c] * 2 * h->bond[c + 1];
+  LaunchHooks* hk = &h->prof.hooks;
+  hook_before(hk, MPS_KCLASS_OTHER, (double)cnt * sizeof(T), 0);
+  CUTRY(h, norm2_sum<T>((const T*)h->site[c], cnt, h->d_partial, kNormParts, h->d_scalar, h->stream), "norm");
+  hook_after(hk, MPS_KCLASS_OTHER, 2);
+  CUTRY(h, cudaMemcpyAsync(out, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm");
+  return check_device_error(h);
+}
+
+// site data of handle x as complex128 (converted into scratch when needed)
+const c128* site_c128(mps_t x, int i, c128* scratch, cudaStream_t s) {
+  if (x->prec == MPS_PREC_FP64) return (const c128*)x->site[i];
+  int64_t cnt = (int64_t)x->bond[i] * 2 * x->bond[i + 1];
+  convert<c128, c64>((const c64*)x->site[i], scratch, cnt, s);
+  return scratch;
+}
+
+int ensure_transfer_scratch(mps_t h, size_t need) {
+  if (h->E_elems >= need) return MPS_OK;
+  void* p = dev_alloc(h, need * sizeof(c128));
+  if (!p) return fail(h, MPS_E_NOMEM, "transfer-matrix scratch allocation failed");
+  h->d_E = (c128*)p;
+  h->E_elems = need;
+  return MPS_OK;
+}
+
+// <a|b> by transfer matrices in FP64, computed on a's stream with a's scratch
+int overlap_impl(mps_t a, mps_t b, mps_c128* out) {
+  const int n = a->n;
+  size_t cap = 0;
+  for (int i = 0; i < n; ++i) {
+    cap = std::max(cap, (size_t)a->capb[i] * 2 * a->capb[i + 1]);
+    cap = std::max(cap, (size_t)b->capb[i] * 2 * b->capb[i + 1]);
+  }
+  size_t eb = 0;
+  for (int i = 0; i <= n; ++i) eb = std::max(eb, (size_t)a->capb[i] * b->capb[i]);
+  size_t tmpb = 0;
+  for (int i = 0; i < n; ++i) tmpb = std::max(tmpb, (size_t)a->capb[i] * b->capb[i + 1]);
+  size_t need = 2 * eb + tmpb + 2 * cap + 4;
+  int rc = ensure_transfer_scratch(a, need);
+  if (rc) return rc;
+  c128* E0 = a->d_E;
+  c128* E1 = E0 + eb;
+  c128* tmp = E1 + eb;
+  c128* sa = tmp + tmpb;
+  c128* sb = sa + cap;
+  cudaStream_t s = a->stream;
+  if (b->stream != s) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(a, e, "overlap sync");
+  }
+  c128 one = mk<double>(1, 0);
+  CUTRY(a, cudaMemcpyAsync(E0, &one, sizeof(c128), cudaMemcpyHostToDevice, s), "overlap");
+  LaunchHooks* hk = &a->prof.hooks;
+  for (int i = 0; i < n; ++i) {
+    const int la = a->bond[i], ra = a->bond[i + 1], lb = b->bond[i], rb = b->bond[i + 1];
+    hook_before(hk, MPS_KCLASS_OTHER, 0, 16.0 * la * lb * rb + 16.0 * ra * la * rb);
+    const c128* A = site_c128(a, i, sa, s);
+    const c128* B = site_c128(b, i, sb, s);
+    int nl = (a->prec == MPS_PREC_MIXED) + (b->prec == MPS_PREC_MIXED);
+    for (int sg = 0; sg < 2; ++sg) {
+      GemmDesc<c128> d;
+      // tmp (la x rb) = E (la x lb) * B^s (lb x rb)
+      d.M = la;
+      d.N = rb;
+      d.K = lb;
+      d.alpha = mk<double>(1, 0);
+      d.beta = mk<double>(0, 0);
+      d.A = E0;
+      d.lda = la;
+      d.a_row = 0;
+      d.a_conj = 0;
+      d.a_mask = MASK_NONE;
+      d.B = B + sg * rb;
+      d.ldb = 2 * rb;
+      d.b_row = 1;
+      d.b_conj = 0;
+      d.b_mask = MASK_NONE;
+      d.C = tmp;
+      d.ldc = la;
+      CUTRY(a, gemm_simt<c128>(d, s), "overlap gemm");
+      // E1 (ra x rb) (+)= A^s^H (ra x la) * tmp
+      d.M = ra;
+      d.N = rb;
+      d.K = la;
+      d.beta = mk<double>(sg == 0 ? 0 : 1, 0);
+      d.A = A + sg * ra;
+      d.lda = 2 * ra;
+      d.a_row = 0;
+      d.a_conj = 1;
+      d.B = tmp;
+      d.ldb = la;
+      d.b_row = 0;
+      d.C = E1;
+      d.ldc = ra;
+      CUTRY(a, gemm_simt<c128>(d, s), "overlap gemm");
+    }
+    hook_after(hk, MPS_KCLASS_OTHER, 4 + nl);
+    std::swap(E0, E1);
+  }
+  c128 r;
+  CUTRY(a, cudaMemcpyAsync(&r, E0, sizeof(c128), cudaMemcpyDeviceToHost, s), "overlap");
+  rc = check_device_error(a);
+  if (rc) return rc;
+  out->re = r.re;
+  out->im = r.im;
+  return MPS_OK;
+}
+
+bool valid_site(mps_t h, int i) { return i >= 0 && i < h->n; }
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+int mps_version(void) { return 100; }
+
+void mps_config_init(mps_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = MPS_PREC_FP64;
+  cfg->policy = MPS_POLICY_CANON;
+}
+
+int mps_create(mps_t* out, int n, int chi_max) { return mps_create_ex(out, n, chi_max, nullptr); }
+
+int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
+  if (!out) return MPS_E_ARG;
+  *out = nullptr;
+  mps_config cfg;
+  if (cfg_in)
+    cfg = *cfg_in;
+  else
+    mps_config_init(&cfg);
+  if (n < 1 || n > 4096 || chi_max < 1 || chi_max > 65536) return MPS_E_ARG;
+  if (cfg.precision != MPS_PREC_FP64 && cfg.precision != MPS_PREC_MIXED) return MPS_E_ARG;
+  if (cfg.policy != MPS_POLICY_CANON && cfg.policy != MPS_POLICY_LOCAL) return MPS_E_ARG;
+  if (cfg.panel_width < 0 || cfg.panel_width > kMaxNb) return MPS_E_ARG;
+  if ((cfg.alloc == nullptr) != (cfg.free == nullptr)) return MPS_E_ARG;
+  if (cfg.wait_timeout_s < 0) return MPS_E_ARG;
+  mps_s* h = new (std::nothrow) mps_s();
+  if (!h) return MPS_E_NOMEM;
+  h->n = n;
+  h->chi_max = chi_max;
+  h->prec = cfg.precision;
+  h->policy = cfg.policy;
+  h->device = cfg.device;
+  h->ualloc = cfg.alloc;
+  h->ufree = cfg.free;
+  h->actx = cfg.alloc_ctx;
+  h->esz = h->prec == MPS_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+  h->kn.nb = cfg.panel_width > 0 ? cfg.panel_width : kDefaultNb;
+  h->kn.flag_tol = h->prec == MPS_PREC_FP64 ? 1.4901161193847656e-08 : 1e-3;
+  double to = cfg.wait_timeout_s > 0 ? cfg.wait_timeout_s : 10.0;
+  h->kn.timeout_ns = (unsigned long long)(to * 1e9);
+  if (cfg.debug_barrier_extra < 0) {
+    return MPS_E_ARG;
+  }
+  h->kn.barrier_extra = (unsigned)cfg.debug_barrier_extra;
+  h->prof.enabled = (cfg.flags & MPS_FLAG_PROFILE) != 0;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    delete h;
+    return MPS_E_CUDA;
+  }
+  if (h->device < 0 || h->device >= ndev) {
+    delete h;
+    return MPS_E_ARG;
+  }
+  if (cudaSetDevice(h->device) != cudaSuccess) {
+    delete h;
+    return MPS_E_CUDA;
+  }
+  int sms = num_sms();
+  h->kn.G = std::min(sms, kMaxCoop);
+  if (cfg.stream) {
+    h->stream = (cudaStream_t)cfg.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return MPS_E_CUDA;
+    }
+    h->stream = h->own_stream;
+  }
+  h->prof.stream = h->stream;
+  // bond dims and reserved capacities
+  h->bond.assign(n + 1, 1);
+  h->capb.resize(n + 1);
+  int chicap = 1;
+  for (int b = 0; b <= n; ++b) {
+    h->capb[b] = max_bond(n, b, chi_max);
+    chicap = std::max(chicap, h->capb[b]);
+  }
+  h->chicap = chicap;
+  // sites: one allocation
+  std::vector<size_t> off(n);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    off[i] = total;
+    total = align_up(total + h->esz * (size_t)h->capb[i] * 2 * h->capb[i + 1]);
+  }
+  char* sites = (char*)dev_alloc(h, total);
+  if (!sites) {
+    release(h);
+    delete h;
+    return MPS_E_NOMEM;
+  }
+  h->site.resize(n);
+  for (int i = 0; i < n; ++i) h->site[i] = sites + off[i];
+  // workspace: largest split (m, n <= 2 chicap, k <= chicap)
+  h->L = ws_layout(h->esz, 2 * chicap, 2 * chicap, chicap, h->kn.nb, h->kn.G, h->ldw, h->ldq);
+  h->ws = (char*)dev_alloc(h, h->L.total);
+  h->d_partial = (double*)dev_alloc(h, sizeof(double) * (kNormParts + 8));
+  h->d_disclog = (double*)dev_alloc(h, sizeof(double) * kDiscLog);
+  h->d_vec = (c128*)dev_alloc(h, sizeof(c128) * (2 * (size_t)chicap + 2));
+  if (!h->ws || !h->d_partial || !h->d_disclog || !h->d_vec) {
+    release(h);
+    delete h;
+    return MPS_E_NOMEM;
+  }
+  h->d_scalar = h->d_partial + kNormParts;
+  cudaError_t e = cudaMemsetAsync(h->ws + h->L.bar, 0, 16, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.err, 0, 16, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_scalar, 0, 8 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sites, 0, total, h->stream);
+  // |0...0>: every site (1, 2, 1) = [1, 0]
+  if (e == cudaSuccess) {
+    std::vector<char> one(h->esz, 0);
+    if (h->prec == MPS_PREC_FP64) {
+      c128 v = mk<double>(1, 0);
+      memcpy(one.data(), &v, sizeof v);
+    } else {
+      c64 v = mk<float>(1, 0);
+      memcpy(one.data(), &v, sizeof v);
+    }
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(h->site[i], one.data(), h->esz, cudaMemcpyHostToDevice, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    release(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? MPS_E_NOMEM : MPS_E_CUDA;
+  }
+  h->centre = 0;
+  *out = h;
+  return MPS_OK;
+}
+
+int mps_destroy(mps_t h) {
+  if (!h) return MPS_OK;
+  cudaSetDevice(h->device);
+  release(h);
+  delete h;
+  return MPS_OK;
+}
+
+const char* mps_last_error(mps_t h) {
+  if (!h) return "null handle";
+  return h->msg.c_str();
+}
+
+int mps_set_stream(mps_t h, void* stream) {
+  if (!h) return MPS_E_ARG;
+  cudaStream_t ns = stream ? (cudaStream_t)stream : h->own_stream;
+  if (!ns) return fail(h, MPS_E_ARG, "no stream to fall back to");
+  if (ns != h->stream) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_stream");
+  }
+  h->stream = ns;
+  h->prof.stream = ns;
+  return MPS_OK;
+}
+
+int mps_sync(mps_t h) {
+  if (!h) return MPS_E_ARG;
+  if (h->status != MPS_OK) return h->status;
+  cudaSetDevice(h->device);
+  return check_device_error(h);
+}
+
+int mps_apply_1q(mps_t h, int site, const mps_c128 u[4]) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!valid_site(h, site) || !u) return fail(h, MPS_E_ARG, "apply_1q: bad site or gate");
+  return h->prec == MPS_PREC_FP64 ? apply_1q_t<c128>(h, site, u) : apply_1q_t<c64>(h, site, u);
+}
+
+int mps_apply_2q(mps_t h, int site, const mps_c128 g[16], int chi_max) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (site < 0 || site + 1 >= h->n || !g) return fail(h, MPS_E_ARG, "apply_2q: bad site or gate");
+  if (chi_max > h->chi_max) return fail(h, MPS_E_ARG, "apply_2q: chi_max above the handle's");
+  int chi = chi_max <= 0 ? h->chi_max : chi_max;
+  return h->prec == MPS_PREC_FP64 ? apply_2q_t<c128>(h, site, g, chi) : apply_2q_t<c64>(h, site, g, chi);
+}
+
+static const mps_c128* swap_gate() {
+  static mps_c128 g[16];
+  static bool init = false;
+  if (!init) {
+    memset(g, 0, sizeof g);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) g[(2 * b + a) * 4 + (2 * a + b)].re = 1.0;
+    init = true;
+  }
+  return g;
+}
+
+int mps_swap(mps_t h, int site, int chi_max) { return mps_apply_2q(h, site, swap_gate(), chi_max); }
+
+int mps_apply_2q_routed(mps_t h, int q1, int q2, const mps_c128 g[16], int chi_max) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (q1 < 0 || q2 < 0 || q1 >= h->n || q2 >= h->n || q1 == q2 || !g)
+    return fail(h, MPS_E_ARG, "apply_2q_routed: bad positions or gate");
+  mps_c128 gg[16];
+  memcpy(gg, g, sizeof gg);
+  if (q1 > q2) {
+    // the same gate with its two qubits listed in the other order: S g S
+    const mps_c128* S = swap_gate();
+    mps_c128 t[16];
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) {
+        double re = 0, im = 0;
+        for (int x = 0; x < 4; ++x)
+          for (int y = 0; y < 4; ++y) {
+            double sr = S[r * 4 + x].re * S[y * 4 + c].re;
+            if (sr == 0.0) continue;
+            re += sr * g[x * 4 + y].re;
+            im += sr * g[x * 4 + y].im;
+          }
+        t[r * 4 + c].re = re;
+        t[r * 4 + c].im = im;
+      }
+    memcpy(gg, t, sizeof gg);
+    std::swap(q1, q2);
+  }
+  for (int b = q1; b < q2 - 1; ++b) {
+    rc = mps_swap(h, b, chi_max);
+    if (rc) return rc;
+  }
+  rc = mps_apply_2q(h, q2 - 1, gg, chi_max);
+  if (rc) return rc;
+  for (int b = q2 - 2; b >= q1; --b) {
+    rc = mps_swap(h, b, chi_max);
+    if (rc) return rc;
+  }
+  return MPS_OK;
+}
+
+int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count, int chi_max) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (count < 0 || (count > 0 && (!sites || !gates))) return fail(h, MPS_E_ARG, "apply_layer: bad arrays");
+  if (h->policy != MPS_POLICY_LOCAL) return fail(h, MPS_E_STATE, "apply_layer needs MPS_POLICY_LOCAL");
+  std::vector<char> used(h->n, 0);
+  for (int j = 0; j < count; ++j) {
+    int s = sites[j];
+    if (s < 0 || s + 1 >= h->n) return fail(h, MPS_E_ARG, "apply_layer: bad site");
+    if (used[s] || used[s + 1]) return fail(h, MPS_E_ARG, "apply_layer: bonds overlap");
+    used[s] = used[s + 1] = 1;
+  }
+  for (int j = 0; j < count; ++j) {
+    rc = mps_apply_2q(h, sites[j], gates + 16 * j, chi_max);
+    if (rc) return rc;
+  }
+  return MPS_OK;
+}
+
+int mps_amplitude(mps_t h, const uint8_t* bits, mps_c128* out) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!bits || !out) return fail(h, MPS_E_ARG, "amplitude: null pointer");
+  for (int i = 0; i < h->n; ++i)
+    if (bits[i] > 1) return fail(h, MPS_E_ARG, "amplitude: bits must be 0 or 1");
+  return h->prec == MPS_PREC_FP64 ? amplitude_t<c128>(h, bits, out) : amplitude_t<c64>(h, bits, out);
+}
+
+int mps_fidelity_estimate(mps_t h, double* out) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!out) return fail(h, MPS_E_ARG, "fidelity: null pointer");
+  if (h->policy == MPS_POLICY_CANON)
+    return h->prec == MPS_PREC_FP64 ? centre_norm_t<c128>(h, out) : centre_norm_t<c64>(h, out);
+  mps_c128 o;
+  rc = overlap_impl(h, h, &o);
+  if (rc) return rc;
+  *out = o.re;
+  return MPS_OK;
+}
+
+int mps_overlap(mps_t a, mps_t b, mps_c128* out) {
+  int rc = usable(a);
+  if (rc) return rc;
+  rc = usable(b);
+  if (rc) return rc;
+  if (!out || a->n != b->n || a->device != b->device) return fail(a, MPS_E_ARG, "overlap: incompatible handles");
+  return overlap_impl(a, b, out);
+}
+
+int mps_bond_dims(mps_t h, int* out) {
+  if (!h || !out) return MPS_E_ARG;
+  for (int i = 0; i <= h->n; ++i) out[i] = h->bond[i];
+  return MPS_OK;
+}
+
+int mps_get_site(mps_t h, int site, int host_fmt, void* host, size_t cap_elems) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!valid_site(h, site) || !host || (host_fmt != MPS_HOST_C128 && host_fmt != MPS_HOST_C64))
+    return fail(h, MPS_E_ARG, "get_site: bad argument");
+  int64_t cnt = (int64_t)h->bond[site] * 2 * h->bond[site + 1];
+  if ((size_t)cnt > cap_elems) return fail(h, MPS_E_ARG, "get_site: host buffer too small");
+  const bool same = (host_fmt == MPS_HOST_C128) == (h->prec == MPS_PREC_FP64);
+  const void* src = h->site[site];
+  size_t hsz = host_fmt == MPS_HOST_C128 ? sizeof(c128) : sizeof(c64);
+  if (!same) {
+    LaunchHooks* hk = &h->prof.hooks;
+    hook_before(hk, MPS_KCLASS_OTHER, (double)cnt * (h->esz + hsz), 0);
+    cudaError_t e;
+    char* stage = h->ws + h->L.W;
+    if (host_fmt == MPS_HOST_C128)
+      e = convert<c128, c64>((const c64*)src, (c128*)stage, cnt, h->stream);
+    else
+      e = convert<c64, c128>((const c128*)src, (c64*)stage, cnt, h->stream);
+    hook_after(hk, MPS_KCLASS_OTHER, 1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_site convert");
+    src = stage;
+  }
+  CUTRY(h, cudaMemcpyAsync(host, src, hsz * cnt, cudaMemcpyDeviceToHost, h->stream), "get_site copy");
+  return check_device_error(h);
+}
+
+int mps_set_site(mps_t h, int site, int chi_l, int chi_r, int host_fmt, const void* host) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!valid_site(h, site) || !host || (host_fmt != MPS_HOST_C128 && host_fmt != MPS_HOST_C64))
+    return fail(h, MPS_E_ARG, "set_site: bad argument");
+  if (chi_l < 1 || chi_r < 1 || chi_l > h->capb[site] || chi_r > h->capb[site + 1])
+    return fail(h, MPS_E_ARG, "set_site: bond dims outside the reserved capacity");
+  if ((site == 0 && chi_l != 1) || (site == h->n - 1 && chi_r != 1))
+    return fail(h, MPS_E_ARG, "set_site: boundary bonds must be 1");
+  int64_t cnt = (int64_t)chi_l * 2 * chi_r;
+  const bool same = (host_fmt == MPS_HOST_C128) == (h->prec == MPS_PREC_FP64);
+  size_t hsz = host_fmt == MPS_HOST_C128 ? sizeof(c128) : sizeof(c64);
+  if (same) {
+    CUTRY(h, cudaMemcpyAsync(h->site[site], host, hsz * cnt, cudaMemcpyHostToDevice, h->stream), "set_site copy");
+  } else {
+    char* stage = h->ws + h->L.W;
+    CUTRY(h, cudaMemcpyAsync(stage, host, hsz * cnt, cudaMemcpyHostToDevice, h->stream), "set_site copy");
+    LaunchHooks* hk = &h->prof.hooks;
+    hook_before(hk, MPS_KCLASS_OTHER, (double)cnt * (h->esz + hsz), 0);
+    cudaError_t e;
+    if (host_fmt == MPS_HOST_C128)
+      e = convert<c64, c128>((const c128*)stage, (c64*)h->site[site], cnt, h->stream);
+    else
+      e = convert<c128, c64>((const c64*)stage, (c128*)h->site[site], cnt, h->stream);
+    hook_after(hk, MPS_KCLASS_OTHER, 1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_site convert");
+  }
+  h->bond[site] = chi_l;
+  h->bond[site + 1] = chi_r;
+  return MPS_OK;
+}
+
+int mps_set_centre(mps_t h, int centre) {
+  if (!h) return MPS_E_ARG;
+  if (!valid_site(h, centre)) return fail(h, MPS_E_ARG, "set_centre: bad site");
+  h->centre = centre;
+  return MPS_OK;
+}
+
+int mps_get_centre(mps_t h, int* out) {
+  if (!h || !out) return MPS_E_ARG;
+  *out = h->centre;
+  return MPS_OK;
+}
+
+int mps_move_centre(mps_t h, int target) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!valid_site(h, target)) return fail(h, MPS_E_ARG, "move_centre: bad site");
+  return h->prec == MPS_PREC_FP64 ? move_centre_t<c128>(h, target) : move_centre_t<c64>(h, target);
+}
+
+int mps_discarded_weight(mps_t h, double* total, long long* count) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!total || !count) return fail(h, MPS_E_ARG, "discarded_weight: null pointer");
+  CUTRY(h, cudaMemcpyAsync(total, h->d_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "discarded");
+  rc = check_device_error(h);
+  if (rc) return rc;
+  *count = h->nsplit;
+  return MPS_OK;
+}
+
+int mps_kernel_stats(mps_t h, mps_kstat* out) {
+  if (!h || !out) return MPS_E_ARG;
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "kernel_stats");
+  h->prof.drain();
+  for (int c = 0; c < MPS_KCLASS_COUNT; ++c) out[c] = h->prof.stat[c];
+  return MPS_OK;
+}
+
+int mps_kernel_stats_reset(mps_t h) {
+  if (!h) return MPS_E_ARG;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  h->prof.drain();
+  memset(h->prof.stat, 0, sizeof(h->prof.stat));
+  return MPS_OK;
+}
+
+// ---- raw-pointer two-site call
+int mps_two_site_workspace(int precision, int chi_l, int chi_m, int chi_r, int chi_max, size_t* bytes) {
+  if (!bytes || chi_l < 1 || chi_m < 1 || chi_r < 1 || chi_max < 1) return MPS_E_ARG;
+  if (precision != MPS_PREC_FP64 && precision != MPS_PREC_MIXED) return MPS_E_ARG;
+  size_t esz = precision == MPS_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+  int m = 2 * chi_l, n = 2 * chi_r, k = std::min(std::min(m, n), chi_max);
+  int64_t ldw, ldq;
+  WsLayout L = ws_layout(esz, m, n, k, kDefaultNb, kMaxCoop, ldw, ldq);
+  *bytes = L.total;
+  return MPS_OK;
+}
+
+int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_max, const void* A, const void* B,
+                       const mps_c128 g[16], void* A_out, void* B_out, double* discarded_dev, void* workspace,
+                       size_t ws_bytes, void* stream) {
+  if (!A || !B || !g || !A_out || !B_out || !workspace) return MPS_E_ARG;
+  size_t need = 0;
+  int rc = mps_two_site_workspace(precision, chi_l, chi_m, chi_r, chi_max, &need);
+  if (rc) return rc;
+  if (ws_bytes < need || ((uintptr_t)workspace % kAlign) != 0) return MPS_E_ARG;
+  size_t esz = precision == MPS_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+  int m = 2 * chi_l, n = 2 * chi_r, k = std::min(std::min(m, n), chi_max);
+  int64_t ldw, ldq;
+  WsLayout L = ws_layout(esz, m, n, k, kDefaultNb, kMaxCoop, ldw, ldq);
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)workspace;
+  if (cudaMemsetAsync(base + L.bar, 0, 16, s) != cudaSuccess) return MPS_E_CUDA;
+  if (cudaMemsetAsync(base + L.err, 0, 16, s) != cudaSuccess) return MPS_E_CUDA;
+  Knobs kn;
+  kn.nb = kDefaultNb;
+  kn.G = std::min(num_sms(), kMaxCoop);
+  kn.flag_tol = precision == MPS_PREC_FP64 ? 1.4901161193847656e-08 : 1e-3;
+  kn.timeout_ns = 10000000000ull;
+  kn.barrier_extra = 0;
+  double* slot = discarded_dev ? discarded_dev : (double*)(base + L.disc);
+  cudaError_t e;
+  if (precision == MPS_PREC_FP64) {
+    c128 gt[16];
+    gate_to_T<c128>(g, 16, gt);
+    e = two_site_core<c128>(ws_views<c128>(base, L, ldw, ldq), kn, chi_l, chi_m, chi_r, chi_max, (const c128*)A,
+                            (const c128*)B, gt, (c128*)A_out, (c128*)B_out, slot, nullptr, s, nullptr);
+  } else {
+    c64 gt[16];
+    gate_to_T<c64>(g, 16, gt);
+    e = two_site_core<c64>(ws_views<c64>(base, L, ldw, ldq), kn, chi_l, chi_m, chi_r, chi_max, (const c64*)A,
+                           (const c64*)B, gt, (c64*)A_out, (c64*)B_out, slot, nullptr, s, nullptr);
+  }
+  (void)k;
+  return e == cudaSuccess ? MPS_OK : MPS_E_CUDA;
+}
+
+}  // extern "C"

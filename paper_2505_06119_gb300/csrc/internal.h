@@ -1,0 +1,142 @@
+// Internal interfaces between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mpsg {
+
+// ---------------------------------------------------------------------------
+// Generic complex GEMM on the CUDA cores:  C = alpha * opA * opB + beta * C.
+// C is column-major (ldc).  A is the M x K operand, B the K x N operand, each
+// read through a "stored" view: element (i, k) of A is
+//     a_row ? A[i*lda + k] : A[i + k*lda]            (conjugated if a_conj)
+// and element (k, j) of B is
+//     b_row ? B[k*ldb + j] : B[k + j*ldb]            (conjugated if b_conj).
+// a_mask selects a structured operand, tested in the stored column-major
+// coordinates (r, c) = a_row ? (k, i) : (i, k):
+//     MASK_UNIT_LOWER: r > c -> stored, r == c -> 1, r < c -> 0  (reflectors V)
+//     MASK_UPPER:      r <= c -> stored, else 0                   (R factor)
+enum { MASK_NONE = 0, MASK_UNIT_LOWER = 1, MASK_UPPER = 2 };
+
+template <typename T>
+struct GemmDesc {
+  int M, N, K;
+  T alpha, beta;
+  const T* A;
+  int64_t lda;
+  int a_row, a_conj, a_mask;
+  const T* B;
+  int64_t ldb;
+  int b_row, b_conj, b_mask;
+  T* C;
+  int64_t ldc;
+};
+
+template <typename T>
+cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s);
+
+// theta contraction with the gate epilogue (Sec. III-B.1 + III-C.2):
+//   X[(l,c),(d,r)] = sum_mu A[l,c,mu] B[mu,d,r]
+//   W[(b*chi_r + r)*ldw + 2l + a] = sum_{cd} g[2a+b][2c+d] X[(l,c),(d,r)]
+// A, B row-major sites; W column-major (2 chi_l) x (2 chi_r).
+template <typename T>
+cudaError_t theta_gemm_simt(int chi_l, int chi_m, int chi_r, const T* A, const T* B, const T* g16,
+                            T* W, int64_t ldw, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Elementwise / data movement kernels
+template <typename T>
+cudaError_t apply_1q(T* site, int chi_l, int chi_r, const T* u4, cudaStream_t s);
+// dst (col-major, ldd) = src (row-major rows x cols, lds), optionally conjugated
+template <typename T>
+cudaError_t transpose_copy(const T* src, int64_t lds, T* dst, int64_t ldd, int rows, int cols,
+                           int conj, cudaStream_t s);
+// dst[r*ldd + c] = src[r*lds + c] (conj optional): strided 2D copy, same orientation
+template <typename T>
+cudaError_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int rows, int cols, int conj,
+                   cudaStream_t s);
+// Left split: site (row-major m x k, ld k) = Q (col-major m x k, ldq)
+// Right split: site[kk*n + c] = R[kk, pos(c)] with pos = inverse of jpvt
+// (R: first k rows of column-major W, upper trapezoidal; zero below).
+template <typename T>
+cudaError_t split_right(const T* W, int64_t ldw, const int* jpvt, int* inv_scratch, int k, int n,
+                        T* site, cudaStream_t s);
+template <typename T>
+cudaError_t set_identity(T* Q, int64_t ldq, int m, int k, cudaStream_t s);
+template <typename TO, typename TI>
+cudaError_t convert(const TI* src, TO* dst, int64_t count, cudaStream_t s);
+// sum |x_i|^2 in FP64, deterministic, result to *out (device)
+template <typename T>
+cudaError_t norm2_sum(const T* x, int64_t count, double* partial, int npart, double* out,
+                      cudaStream_t s);
+// out (1 x cols) = v (1 x rows) * M (row-major rows x cols, ld), T accumulation in FP64
+template <typename T>
+cudaError_t vecmat(const c128* v, const T* M, int64_t ld, int rows, int cols, c128* out,
+                   cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Pivoted / plain blocked Householder QR of a column-major m x n matrix W.
+
+template <typename T>
+struct QrPlan {
+  int m, n, k;     // k reflectors
+  int nb;          // panel width
+  int pivot;       // 1 = column-pivoted (QP3), 0 = plain QR
+  T* W;
+  int64_t ldw;
+  // outputs / scratch (device)
+  T* tau;          // k
+  int* jpvt;       // n
+  T* Tfac;         // ceil(k/nb) * nb * nb, per-panel triangular factors (column-major nb x nb)
+  T* F;            // n x nb row-major (ld nb)
+  double* vn1;     // n
+  double* vn2;     // n
+  // reduction scratch for the cooperative panel kernel
+  double* red_norm;   // G
+  c128* red_w;        // G * nb
+  double* red_argv;   // G
+  int* red_argi;      // G
+  c128* alpha_slot;   // 1
+  unsigned* bar;      // 2 (zeroed once)
+  int* err;           // device error word
+  double* discarded;  // out: ||W[k:m, k:n]||_F^2 (pivot mode)
+  double* disc_total; // optional: discarded is also added here
+  T* Y;               // nb * max(n, k) scratch for block-reflector GEMMs
+  T* Z;               // nb * max(n, k)
+  int G;              // cooperative grid size cap
+  double flag_tol;    // norm-downdate recompute threshold
+  unsigned long long timeout_ns;
+  unsigned barrier_extra;  // 0 normally; >0 only to exercise the timeout path
+};
+
+struct LaunchHooks;  // profiling hooks (engine.cu)
+
+template <typename T>
+cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks);
+// Q (column-major m x k, ldq) = H_0 ... H_{k-1} I[:, :k]
+template <typename T>
+cudaError_t qr_form_q(const QrPlan<T>& p, T* Q, int64_t ldq, cudaStream_t s, LaunchHooks* hooks);
+
+int num_sms();
+
+// Profiling hooks: the engine passes these so every launch is counted and,
+// when profiling, bracketed by CUDA events.
+// Every kernel launch of the library sits between hook_before and
+// hook_after; `nlaunch` is the number of kernels launched in between.
+struct LaunchHooks {
+  void (*before)(LaunchHooks* h, int kclass, double bytes, double flops);
+  void (*after)(LaunchHooks* h, int kclass, int nlaunch);
+  void* ctx;
+};
+
+inline void hook_before(LaunchHooks* h, int kclass, double bytes, double flops) {
+  if (h && h->before) h->before(h, kclass, bytes, flops);
+}
+inline void hook_after(LaunchHooks* h, int kclass, int nlaunch) {
+  if (h && h->after) h->after(h, kclass, nlaunch);
+}
+
+}  // namespace mpsg

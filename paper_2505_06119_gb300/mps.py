@@ -1,0 +1,187 @@
+"""Thin Python binding of the C ABI: one class per handle, argument marshalling only.
+
+Every operation runs in the CUDA library (include/mps.h); this module only
+converts NumPy arrays to the ABI's plain arrays and checks return codes.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+class MPSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (L.ERROR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _gate(g, n):
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.complex128).reshape(-1))
+    if g.size != n:
+        raise ValueError("gate must have %d entries" % n)
+    arr = (L.mps_c128 * n)()
+    for i in range(n):
+        arr[i].re = g[i].real
+        arr[i].im = g[i].imag
+    return arr
+
+
+def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile=False,
+           wait_timeout_s=0.0, device=0, debug_barrier_extra=0):
+    lib = L.load()
+    cfg = L.mps_config()
+    lib.mps_config_init(ctypes.byref(cfg))
+    cfg.precision = {"fp64": L.MPS_PREC_FP64, "mixed": L.MPS_PREC_MIXED}[precision]
+    cfg.policy = {"canon": L.MPS_POLICY_CANON, "local": L.MPS_POLICY_LOCAL}[policy]
+    cfg.panel_width = panel_width
+    cfg.stream = stream
+    cfg.flags = L.MPS_FLAG_PROFILE if profile else 0
+    cfg.wait_timeout_s = wait_timeout_s
+    cfg.device = device
+    cfg.debug_barrier_extra = debug_barrier_extra
+    return cfg
+
+
+class MPS:
+    """An n-qubit MPS on the GPU (handle of the C library)."""
+
+    def __init__(self, n, chi_max, precision="fp64", policy="canon", **kw):
+        self.lib = L.load()
+        self.n = n
+        self.chi_max = chi_max
+        self.precision = precision
+        self.policy = policy
+        cfg = config(precision, policy, **kw)
+        h = ctypes.c_void_p()
+        rc = self.lib.mps_create_ex(ctypes.byref(h), n, chi_max, ctypes.byref(cfg))
+        if rc != L.MPS_OK:
+            raise MPSError(rc, "mps_create_ex failed")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != L.MPS_OK:
+            msg = self.lib.mps_last_error(self.h)
+            raise MPSError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- gates
+    def apply_1q(self, q, u):
+        self._check(self.lib.mps_apply_1q(self.h, q, _gate(u, 4)))
+
+    def apply_2q(self, i, g, chi_max=0):
+        self._check(self.lib.mps_apply_2q(self.h, i, _gate(g, 16), chi_max))
+
+    def swap(self, i, chi_max=0):
+        self._check(self.lib.mps_swap(self.h, i, chi_max))
+
+    def apply_2q_routed(self, q1, q2, g, chi_max=0):
+        self._check(self.lib.mps_apply_2q_routed(self.h, q1, q2, _gate(g, 16), chi_max))
+
+    def apply_layer(self, sites, gates, chi_max=0):
+        cnt = len(sites)
+        s = (ctypes.c_int * max(cnt, 1))(*sites)
+        g = _gate(np.concatenate([np.asarray(x).reshape(-1) for x in gates]) if cnt else np.zeros(16), 16 * max(cnt, 1))
+        self._check(self.lib.mps_apply_layer(self.h, s, g, cnt, chi_max))
+
+    def run(self, ops, chi_max=0):
+        for op in ops:
+            if op[0] == "1q":
+                self.apply_1q(op[1], op[2])
+            elif abs(op[1] - op[2]) == 1 and op[1] < op[2]:
+                self.apply_2q(op[1], op[3], chi_max)
+            else:
+                self.apply_2q_routed(op[1], op[2], op[3], chi_max)
+
+    # ---- observables
+    def amplitude(self, bits):
+        b = (ctypes.c_uint8 * self.n)(*[int(x) for x in bits])
+        out = L.mps_c128()
+        self._check(self.lib.mps_amplitude(self.h, b, ctypes.byref(out)))
+        return complex(out.re, out.im)
+
+    def fidelity(self):
+        out = ctypes.c_double()
+        self._check(self.lib.mps_fidelity_estimate(self.h, ctypes.byref(out)))
+        return out.value
+
+    def overlap(self, other):
+        out = L.mps_c128()
+        self._check(self.lib.mps_overlap(self.h, other.h, ctypes.byref(out)))
+        return complex(out.re, out.im)
+
+    def bond_dims(self):
+        arr = (ctypes.c_int * (self.n + 1))()
+        self._check(self.lib.mps_bond_dims(self.h, arr))
+        return list(arr)
+
+    def get_site(self, i, fmt="c128"):
+        b = self.bond_dims()
+        shape = (b[i], 2, b[i + 1])
+        dt = np.complex128 if fmt == "c128" else np.complex64
+        out = np.empty(shape, dtype=dt)
+        code = L.MPS_HOST_C128 if fmt == "c128" else L.MPS_HOST_C64
+        self._check(self.lib.mps_get_site(self.h, i, code, out.ctypes.data, out.size))
+        return out
+
+    def set_site(self, i, a):
+        a = np.asarray(a)
+        if a.dtype == np.complex64:
+            code = L.MPS_HOST_C64
+        else:
+            a = a.astype(np.complex128)
+            code = L.MPS_HOST_C128
+        a = np.ascontiguousarray(a)
+        self._check(self.lib.mps_set_site(self.h, i, a.shape[0], a.shape[2], code, a.ctypes.data))
+
+    def set_sites(self, sites, centre=0):
+        for i, s in enumerate(sites):
+            self.set_site(i, s)
+        self._check(self.lib.mps_set_centre(self.h, centre))
+
+    def centre(self):
+        c = ctypes.c_int()
+        self._check(self.lib.mps_get_centre(self.h, ctypes.byref(c)))
+        return c.value
+
+    def move_centre(self, target):
+        self._check(self.lib.mps_move_centre(self.h, target))
+
+    def discarded(self):
+        t = ctypes.c_double()
+        c = ctypes.c_longlong()
+        self._check(self.lib.mps_discarded_weight(self.h, ctypes.byref(t), ctypes.byref(c)))
+        return t.value, c.value
+
+    def sync(self):
+        self._check(self.lib.mps_sync(self.h))
+
+    def set_stream(self, stream_ptr):
+        self._check(self.lib.mps_set_stream(self.h, stream_ptr))
+
+    def kernel_stats(self):
+        arr = (L.mps_kstat * L.KCLASS_COUNT)()
+        self._check(self.lib.mps_kernel_stats(self.h, arr))
+        return {name: {"launches": arr[i].launches, "ms": arr[i].ms, "alg_bytes": arr[i].alg_bytes,
+                       "alg_flops": arr[i].alg_flops} for i, name in enumerate(L.KCLASS)}
+
+    def kernel_stats_reset(self):
+        self._check(self.lib.mps_kernel_stats_reset(self.h))

@@ -1,0 +1,146 @@
+"""GPU checks of the ABI's non-arithmetic behaviour: the raw-pointer two-site
+call on caller-owned (PyTorch) buffers, the optional device allocator, the
+bounded-wait error path, and launch accounting."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from workloads import gates, states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def test_raw_two_site_call_matches_handle_path():
+    import torch
+
+    from paper_2505_06119_gb300 import MPS, _lib as L
+    from paper_2505_06119_gb300.mps import _gate
+
+    lib = L.load()
+    rng = np.random.default_rng(3)
+    cl, cm, cr, chi = 33, 20, 17, 24
+    a = states.complex_gaussian(rng, (cl, 2, cm))
+    b = states.complex_gaussian(rng, (cm, 2, cr))
+    g = gates.haar_unitary(rng, 4)
+    for prec, dt, tdt in (("fp64", np.complex128, torch.complex128), ("mixed", np.complex64, torch.complex64)):
+        code = L.MPS_PREC_FP64 if prec == "fp64" else L.MPS_PREC_MIXED
+        dev = torch.device("cuda:0")
+        ta = torch.from_numpy(a.astype(dt)).to(dev)
+        tb = torch.from_numpy(b.astype(dt)).to(dev)
+        k = min(2 * cl, 2 * cr, chi)
+        oa = torch.empty((cl, 2, k), dtype=tdt, device=dev)
+        ob = torch.empty((k, 2, cr), dtype=tdt, device=dev)
+        disc = torch.zeros(1, dtype=torch.float64, device=dev)
+        sz = ctypes.c_size_t()
+        assert lib.mps_two_site_workspace(code, cl, cm, cr, chi, ctypes.byref(sz)) == 0
+        ws = torch.empty(sz.value + 256, dtype=torch.uint8, device=dev)
+        base = (ws.data_ptr() + 255) // 256 * 256
+        stream = torch.cuda.current_stream().cuda_stream
+        rc = lib.mps_two_site_apply(code, cl, cm, cr, chi, ta.data_ptr(), tb.data_ptr(), _gate(g, 16),
+                                    oa.data_ptr(), ob.data_ptr(), disc.data_ptr(), base, sz.value, stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        with MPS(4, max(cl, cm, cr, chi), precision=prec, policy="local") as m:
+            m.set_site(0, np.ones((1, 2, cl)) / np.sqrt(2 * cl))
+            m.set_site(1, a)
+            m.set_site(2, b)
+            m.set_site(3, np.ones((cr, 2, 1)))
+            m.apply_2q(1, g, chi)
+            ha, hb = m.get_site(1), m.get_site(2)
+            hd, _ = m.discarded()
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        assert np.abs(oa.cpu().numpy() - ha).max() <= tol
+        assert np.abs(ob.cpu().numpy() - hb).max() <= tol * max(1, np.abs(hb).max())
+        assert disc.item() == pytest.approx(hd, rel=1e-6)
+
+
+def test_allocator_hook_and_nomem():
+    import torch
+
+    from paper_2505_06119_gb300 import _lib as L
+
+    lib = L.load()
+    live = {}
+
+    def alloc(size, ctx):
+        p = torch.cuda.caching_allocator_alloc(size, 0, torch.cuda.current_stream())
+        live[p] = size
+        return p
+
+    def free(p, ctx):
+        live.pop(p)
+        torch.cuda.caching_allocator_delete(p)
+
+    fa, ff = L.ALLOC_FN(alloc), L.FREE_FN(free)
+    cfg = L.mps_config()
+    lib.mps_config_init(ctypes.byref(cfg))
+    cfg.alloc, cfg.free = fa, ff
+    h = ctypes.c_void_p()
+    assert lib.mps_create_ex(ctypes.byref(h), 8, 8, ctypes.byref(cfg)) == 0
+    assert len(live) > 0
+    u = (L.mps_c128 * 4)()
+    hg = gates.hadamard().reshape(-1)
+    for i in range(4):
+        u[i].re, u[i].im = hg[i].real, hg[i].imag
+    assert lib.mps_apply_1q(h, 0, u) == 0
+    assert lib.mps_swap(h, 0, 0) == 0
+    assert lib.mps_sync(h) == 0
+    assert lib.mps_destroy(h) == 0
+    assert live == {}
+
+    calls = {"n": 0}
+
+    def failing(size, ctx):
+        calls["n"] += 1
+        if calls["n"] >= 2:
+            return None
+        return alloc(size, ctx)
+
+    fa2 = L.ALLOC_FN(failing)
+    cfg.alloc = fa2
+    assert lib.mps_create_ex(ctypes.byref(h), 8, 8, ctypes.byref(cfg)) == L.MPS_E_NOMEM
+    assert live == {}
+
+
+def test_bounded_wait_expiry_is_reported_and_context_survives():
+    """A grid barrier told to wait for one CTA too many gives up after the
+    configured limit; the call reports MPS_E_TIMEOUT, the handle refuses further
+    work, and a fresh handle on the same context works."""
+    from paper_2505_06119_gb300 import MPS, MPSError, _lib as L
+
+    m = MPS(6, 8, precision="fp64", wait_timeout_s=0.05, debug_barrier_extra=1)
+    m.apply_2q(0, gates.haar_unitary(np.random.default_rng(0), 4))
+    with pytest.raises(MPSError) as ei:
+        m.sync()
+    assert ei.value.code == L.MPS_E_TIMEOUT
+    with pytest.raises(MPSError) as ei:
+        m.apply_1q(0, gates.hadamard())
+    assert ei.value.code == L.MPS_E_STATE
+    m.close()
+    with MPS(6, 8, precision="fp64") as m2:
+        m2.apply_1q(0, gates.hadamard())
+        m2.apply_2q(0, gates.cnot())
+        assert abs(m2.amplitude([1, 1, 0, 0, 0, 0]) - 1 / np.sqrt(2)) < 1e-12
+
+
+def test_launch_accounting_and_profile():
+    from paper_2505_06119_gb300 import MPS
+
+    with MPS(8, 16, precision="mixed", profile=True) as m:
+        m.apply_2q(3, gates.haar_unitary(np.random.default_rng(1), 4))
+        m.sync()
+        st = m.kernel_stats()
+        assert st["theta"]["launches"] == 1
+        assert st["panel"]["launches"] >= 1
+        assert st["panel"]["ms"] > 0
+        m.kernel_stats_reset()
+        assert m.kernel_stats()["panel"]["launches"] == 0
