@@ -1,0 +1,422 @@
+"""Benchmark: two-site gate applies/s at chi = 4096, mixed-precision vs FP64 path.
+
+Workload (steady state of a saturated bond, the chi = 4096 configuration):
+an n = 26 chain whose bonds saturate at chi = 4096 (bonds 12, 13, 14 are 4096),
+initialised as a random mixed-canonical MPS (sites left of 12 left-isometries,
+right of 12 right-isometries, site 12 i.i.d. complex Gaussian of unit norm;
+workloads/states.py).  One step = one pass of the whole hot path on bond
+(12, 13) under the canonical policy:
+  * one-qubit Haar gates on sites 12 and 13,
+  * the centre move back to site 12 (LQ of site 13, absorbed into site 12),
+  * the theta contraction with the gate epilogue, the truncated pivoted QR
+    (k = chi), Q formation and the split,
+with the two-qubit gate alternating between a seeded Haar SU(4) gate
+(mps_apply_2q) and a SWAP (mps_swap).  Bond dims are invariant (k = chi), so
+every step is the same amount of work.  Inputs (theta is 512 MiB in c64) are
+larger than L2, so no flush is needed between steps.
+
+`value` is the mixed path's applies/s over all ranks (replicas: one independent
+state per GPU, no collectives on the data path).  The FP64 path runs the same
+steps for a shorter count; the fidelity deviation compares a mixed and an FP64
+state after the same steps.
+
+--impl reference times the CPU oracle (oracle/) on the host cores instead.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CHI = 4096
+N_SITES = 26
+BOND_SITE = 12
+METRIC = "two-site gate applies/s at chi=4096; mixed vs FP64 path at fidelity dev <=1e-6"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_state(chi, n, centre, seed):
+    import numpy as np
+
+    from workloads import states
+
+    bonds = states.max_bond_dims(n, chi)
+    sites = states.random_canonical_mps(n, bonds, centre, seed=seed)
+    return [np.ascontiguousarray(s) for s in sites]
+
+
+def step_gates(steps, seed):
+    import numpy as np
+
+    from workloads import gates
+
+    rng = np.random.default_rng(seed)
+    seq = []
+    for s in range(steps):
+        u1 = gates.haar_unitary(rng, 2)
+        u2 = gates.haar_unitary(rng, 2)
+        g = gates.haar_unitary(rng, 4) if s % 2 == 0 else None  # None = SWAP
+        seq.append((u1, u2, g))
+    return seq
+
+
+def do_step(m, st, i=BOND_SITE):
+    u1, u2, g = st
+    m.apply_1q(i, u1)
+    m.apply_1q(i + 1, u2)
+    if g is None:
+        m.swap(i)
+    else:
+        m.apply_2q(i, g)
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_2505_06119_gb300 import MPS
+
+    chi = args.chi
+    n = N_SITES if chi == CHI else 2 * int(math.log2(chi)) + 2
+    i = n // 2 - 1  # bonds i, i+1, i+2 all equal chi
+    sites = make_state(chi, n, i, seed=1234 + rank)
+    seq = step_gates(max(args.warmup + args.steps, args.fp64_warmup + args.fp64_steps), seed=99 + rank)
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+
+    # --- mixed path, timed with per-kernel-class CUDA events
+    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, profile=True, device=local)
+    m.set_sites([s.astype(np.complex64) for s in sites], centre=i)
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ms, st = time_steps_at(m, seq, args.warmup, args.steps, torch, stream, i)
+    clocks = clk.summary()
+    ms_step = ms / args.steps
+    launches = int(sum(v["launches"] for v in st.values()))
+    panel = st["panel"]
+    peaks, peak_src = load_peaks()
+    achieved = panel["alg_bytes"] / (panel["ms"] * 1e-3) / 1e9 if panel["ms"] > 0 else 0.0
+    m.close()
+
+    # --- FP64 path on the same steps
+    m64 = MPS(n, chi, precision="fp64", policy="canon", stream=sptr, device=local)
+    m64.set_sites(sites, centre=i)
+    ms64, st64 = time_steps_at(m64, seq, args.fp64_warmup, args.fp64_steps, torch, stream, i)
+    ms_step64 = ms64 / args.fp64_steps
+
+    # --- fidelity deviation: a mixed state run through exactly the FP64 steps
+    mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
+    mm.set_sites([s.astype(np.complex64) for s in sites], centre=i)
+    for stp in seq[:args.fp64_warmup + args.fp64_steps]:
+        do_step_at(mm, stp, i)
+    f64 = m64.fidelity()
+    fmx = mm.fidelity()
+    dev_f = abs(fmx - f64) / f64
+    dev_o = None
+    if not args.skip_overlap:
+        o = mm.overlap(m64)
+        dev_o = 1.0 - abs(o) ** 2 / (fmx * f64)
+    mm.close()
+    m64.close()
+
+    # --- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np)
+
+    steps_all = args.steps * ws
+    t_max = ms
+    e2e_v = e2e["value"]
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms, e2e["seconds"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_s = float(t[0]), float(t[1])
+        e2e_v = e2e["steps"] * ws / e2e_s
+    value = steps_all / (t_max * 1e-3)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "applies/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64",
+        "data": "synthetic",
+        "config": {
+            "workload": "steady-state two-site apply on a saturated bond, chi_l=chi_m=chi_r=%d, n=%d, "
+                        "canonical policy (centre move + 1q gates + gate/SWAP alternating per step)" % (chi, n),
+            "chi": chi, "n_sites": n, "bond_site": i, "policy": "canon",
+            "precision": "complex64 bulk, FP64 column norms / reflector norms / pivots",
+            "l2": "inputs larger than L2 (theta %d MiB)" % (((2 * chi) ** 2 * 8) >> 20),
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+        },
+        "fp64_path": {"value": ws * 1e3 / ms_step64, "unit": "applies/s", "ms_per_step": ms_step64,
+                      "steps": args.fp64_steps, "warmup": args.fp64_warmup, "dtype": "c128"},
+        "speedup_vs_fp64": ms_step64 / ms_step,
+        "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o,
+                         "steps": args.fp64_warmup + args.fp64_steps, "f_fp64": f64, "f_mixed": fmx},
+        "roofline": {"bound": "hbm", "kernel": "qr_panel_kernel (pivoted-QR panel: per-step trailing GEMV)",
+                     "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": achieved / peaks.get("hbm_gbs", 1.0), "traffic": None,
+                     "peak_source": peak_src,
+                     "launches_timed": panel["launches"], "kernel_ms_per_step": panel["ms"] / args.steps},
+        "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in st.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": {"value": e2e_v, "unit": "applies/s", "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def do_step_at(m, st, i):
+    do_step(m, st, i)
+
+
+def time_steps_at(m, seq, warmup, steps, torch, stream, i):
+    for st in seq[:warmup]:
+        do_step(m, st, i)
+    m.sync()
+    m.kernel_stats_reset()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for st in seq[warmup:warmup + steps]:
+        do_step(m, st, i)
+    e1.record(stream)
+    m.sync()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), m.kernel_stats()
+
+
+def e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np):
+    """Each step: the two sites come from pinned host memory, the step runs, the two
+    new sites go back to pinned host memory, all through the C ABI."""
+    from paper_2505_06119_gb300 import MPS
+
+    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
+    m.set_sites([s.astype(np.complex64) for s in sites], centre=i)
+    a_h = torch.from_numpy(sites[i].astype(np.complex64)).pin_memory()
+    b_h = torch.from_numpy(sites[i + 1].astype(np.complex64)).pin_memory()
+    a_out = torch.empty_like(a_h).pin_memory()
+    b_out = torch.empty_like(b_h).pin_memory()
+    an, bn, ao, bo = a_h.numpy(), b_h.numpy(), a_out.numpy(), b_out.numpy()
+    steps = max(1, args.e2e_steps)
+    for st in seq[:1]:
+        m.set_site(i, an)
+        m.set_site(i + 1, bn)
+        m.set_centre(i)
+        do_step(m, st, i)
+        m.get_site(i, fmt="c64")
+    m.sync()
+    t0 = time.perf_counter()
+    for st in seq[1:1 + steps]:
+        m.set_site(i, an)
+        m.set_site(i + 1, bn)
+        m.set_centre(i)
+        do_step(m, st, i)
+        ao[...] = m.get_site(i, fmt="c64")
+        bo[...] = m.get_site(i + 1, fmt="c64")
+    m.sync()
+    dt = time.perf_counter() - t0
+    m.close()
+    nbytes = an.nbytes + bn.nbytes
+    return {"value": steps / dt, "seconds": dt, "steps": steps, "h2d": nbytes, "d2h": nbytes}
+
+
+# ---------------------------------------------------------------------------
+def oracle_apply_sample(chi_s, seed):
+    """One oracle step of the same recipe at bond chi_s: returns seconds."""
+    from oracle import mps as omps
+
+    n = 2 * int(math.log2(chi_s)) + 2
+    i = n // 2 - 1
+    sites = make_state(chi_s, n, i, seed)
+    seq = step_gates(2, seed + 1)
+    o = omps.OracleMPS(n, chi_s, "canon")
+    o.set_sites(sites, centre=i)
+    t0 = time.perf_counter()
+    for st in seq:
+        u1, u2, g = st
+        o.apply_1q(i, u1)
+        o.apply_1q(i + 1, u2)
+        if g is None:
+            o.swap(i)
+        else:
+            o.apply_2q(i, g)
+    return (time.perf_counter() - t0) / len(seq)
+
+
+def cpu_baseline(args, budget_s=None):
+    """The oracle as it stands on this host's cores: a bounded sample of the same
+    step recipe at chi = 1024 (an apply at chi = 4096 takes minutes), scaled to the
+    chi = 4096 unit by the cubic work ratio (1024/4096)^3."""
+    from oracle import build as obuild
+    from oracle import qr as oqr
+
+    obuild.build()
+    chi_s = args.cpu_chi
+    secs = oracle_apply_sample(chi_s, seed=7)
+    scale = (chi_s / args.chi) ** 3
+    return {"value": scale / secs, "unit": "applies/s", "cores": oqr.num_threads(), "kind": "oracle",
+            "sample": "2 oracle steps (same recipe: 1q gates, centre move, gate/SWAP, pivoted-QR split) at "
+                      "chi=%d, %.2f s per step; applies/s scaled to chi=%d by (%d/%d)^3" % (
+                          chi_s, secs, args.chi, chi_s, args.chi),
+            "seconds_per_sample_step": secs}
+
+
+def reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    from oracle import qr as oqr
+
+    obuild.build()
+    chi_s = args.cpu_chi
+    if args.warmup > 0:
+        oracle_apply_sample(chi_s, seed=3)
+    times = [oracle_apply_sample(chi_s, seed=11 + s) for s in range(max(1, args.steps))]
+    secs = statistics.mean(times)
+    scale = (chi_s / args.chi) ** 3
+    value = scale / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / scale,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": "steady-state two-site apply on a saturated bond, chi_l=chi_m=chi_r=%d, "
+                               "canonical policy (CPU oracle)" % args.chi, "chi": args.chi},
+        "cpu_baseline": {"value": value, "unit": "applies/s", "cores": oqr.num_threads(), "kind": "oracle",
+                         "sample": "each step: 2 oracle steps of the same recipe at chi=%d, scaled to chi=%d "
+                                   "by (%d/%d)^3" % (chi_s, args.chi, chi_s, args.chi)},
+        "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chi", type=int, default=CHI)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-chi", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-overlap", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -157,6 +157,9 @@ class MPS:
             self.set_site(i, s)
         self._check(self.lib.mps_set_centre(self.h, centre))
 
+    def set_centre(self, centre):
+        self._check(self.lib.mps_set_centre(self.h, centre))
+
     def centre(self):
         c = ctypes.c_int()
         self._check(self.lib.mps_get_centre(self.h, ctypes.byref(c)))

@@ -49,13 +49,11 @@ def test_raw_two_site_call_matches_handle_path():
                                     oa.data_ptr(), ob.data_ptr(), disc.data_ptr(), base, sz.value, stream)
         assert rc == 0
         torch.cuda.synchronize()
-        with MPS(4, max(cl, cm, cr, chi), precision=prec, policy="local") as m:
-            m.set_site(0, np.ones((1, 2, cl)) / np.sqrt(2 * cl))
-            m.set_site(1, a)
-            m.set_site(2, b)
-            m.set_site(3, np.ones((cr, 2, 1)))
-            m.apply_2q(1, g, chi)
-            ha, hb = m.get_site(1), m.get_site(2)
+        with MPS(16, max(cl, cm, cr, chi), precision=prec, policy="local") as m:
+            m.set_site(7, a)  # reserved bonds at 7, 8, 9 are >= 64
+            m.set_site(8, b)
+            m.apply_2q(7, g, chi)
+            ha, hb = m.get_site(7), m.get_site(8)
             hd, _ = m.discarded()
         tol = 1e-12 if prec == "fp64" else 1e-5
         assert np.abs(oa.cpu().numpy() - ha).max() <= tol

@@ -39,6 +39,19 @@ def sites_statevector(m):
     return v.reshape(-1)
 
 
+def placement(cl, cm, cr):
+    """Chain length n and site i whose reserved bonds fit (cl, cm, cr) at i, i+1, i+2."""
+    e = int(np.ceil(np.log2(max(cl, cm, cr, 2)))) + 1
+    return 2 * e + 2, e
+
+
+def load_two_sites(m, i, a, b):
+    """Only sites i, i+1 matter under the local policy; the others keep their
+    (unused) initial content."""
+    m.set_site(i, a)
+    m.set_site(i + 1, b)
+
+
 def oracle_split(a, b, g, chi):
     """Oracle two-site split of sites a, b under gate g (Sec. III-C.2)."""
     cl, cm, cr = a.shape[0], a.shape[2], b.shape[2]
@@ -70,19 +83,18 @@ def test_single_split_fp64_matches_oracle(cl, cm, cr, chi):
     Q and R P^T element by element (tie-free Gaussian input, LOCAL policy so no
     centre move is involved)."""
     rng = np.random.default_rng(cl * 7919 + cm * 31 + cr)
-    n = 4
-    bonds = [1, cl, cm, cr, 1]
-    sites = [states.complex_gaussian(rng, (bonds[i], 2, bonds[i + 1])) for i in range(n)]
+    a = states.complex_gaussian(rng, (cl, 2, cm))
+    b = states.complex_gaussian(rng, (cm, 2, cr))
     g = gates.haar_unitary(rng, 4)
+    n, i = placement(cl, cm, cr)
     chi_cap = max(cl, cm, cr, chi, 4)
     with gpu_mps(n, chi_cap, precision="fp64", policy="local") as m:
-        for i in range(n):
-            m.set_site(i, sites[i])
-        m.apply_2q(1, g, chi)
-        qa = m.get_site(1)
-        rb = m.get_site(2)
+        load_two_sites(m, i, a, b)
+        m.apply_2q(i, g, chi)
+        qa = m.get_site(i)
+        rb = m.get_site(i + 1)
         disc, cnt = m.discarded()
-    qo, ro, do = oracle_split(sites[1], sites[2], g, chi)
+    qo, ro, do = oracle_split(a, b, g, chi)
     k = min(2 * cl, 2 * cr, chi)
     assert qa.shape == (cl, 2, k) and rb.shape == (k, 2, cr)
     scale = max(1.0, np.abs(ro).max())
@@ -98,17 +110,16 @@ def test_single_split_mixed_close_to_oracle(cl, cm, cr, chi):
     Q R P^T matches the oracle's to ~1e-5 relative (FP32 rounding over
     contractions of length <= 2*max(cl, cr))."""
     rng = np.random.default_rng(cl + 1000 * cr + 17)
-    n = 4
-    bonds = [1, cl, cm, cr, 1]
-    sites = [states.complex_gaussian(rng, (bonds[i], 2, bonds[i + 1])) for i in range(n)]
+    a = states.complex_gaussian(rng, (cl, 2, cm))
+    b = states.complex_gaussian(rng, (cm, 2, cr))
     g = gates.haar_unitary(rng, 4)
+    n, i = placement(cl, cm, cr)
     with gpu_mps(n, max(cl, cm, cr, chi, 4), precision="mixed", policy="local") as m:
-        for i in range(n):
-            m.set_site(i, sites[i])
-        m.apply_2q(1, g, chi)
-        qa = m.get_site(1)
-        rb = m.get_site(2)
-    qo, ro, _ = oracle_split(sites[1], sites[2], g, chi)
+        load_two_sites(m, i, a, b)
+        m.apply_2q(i, g, chi)
+        qa = m.get_site(i)
+        rb = m.get_site(i + 1)
+    qo, ro, _ = oracle_split(a, b, g, chi)
     kept_gpu = qa.reshape(2 * cl, -1) @ rb.reshape(rb.shape[0], -1)
     kept_ora = qo.reshape(2 * cl, -1) @ ro.reshape(ro.shape[0], -1)
     rel = np.linalg.norm(kept_gpu - kept_ora) / np.linalg.norm(kept_ora)
@@ -209,7 +220,10 @@ def test_routed_grid_circuit_vs_statevector(prec, tol):
 
 
 def test_routed_truncated_matches_oracle():
-    ops = circuits.grid_rcs(3, 4, 8, seed=11)
+    """Routed grid circuit with truncation.  Haar one-qubit gates keep the column
+    norms free of exact ties (the paper's sqrt gates create ties, where two
+    correct implementations may pick different pivots)."""
+    ops = circuits.grid_rcs(3, 4, 8, seed=11, singles="haar")
     ref = omps.OracleMPS(12, 8, "canon")
     ref.run(ops)
     with gpu_mps(12, 8, precision="fp64") as m:

@@ -179,22 +179,26 @@ def grid_pattern(rows, cols, pat):
     return pairs
 
 
-def grid_rcs(rows, cols, cycles, seed, pattern="ABCDCDAB"):
+def grid_rcs(rows, cols, cycles, seed, pattern="ABCDCDAB", singles="paper"):
     """Random circuit on a rows x cols grid, snaked onto a 1D chain.
 
     Each cycle: a one-qubit gate drawn i.i.d. uniformly from {sqrt(X), sqrt(Y),
     sqrt(W)} on every qubit (App. A), then fSim on every coupler of the cycle's
     pattern (Eq. (fsim)); patterns follow ``pattern`` cyclically (Sec. III-D.2).
     Vertical couplers are non-adjacent in the snake and need routing.
+    ``singles="haar"`` draws Haar SU(2) one-qubit gates instead: the paper's
+    gate set makes exactly equal column norms (pivot ties) common, which a
+    test comparing two implementations pivot for pivot has to avoid.
     """
     rng = np.random.default_rng(seed)
-    singles = [G.sqrt_x(), G.sqrt_y(), G.sqrt_w()]
+    paper = [G.sqrt_x(), G.sqrt_y(), G.sqrt_w()]
     f = G.fsim()
     ops = []
     for cyc in range(cycles):
         for r in range(rows):
             for c in range(cols):
-                ops.append(("1q", snake_position(r, c, cols), singles[int(rng.integers(0, 3))]))
+                u = paper[int(rng.integers(0, 3))] if singles == "paper" else G.haar_unitary(rng, 2)
+                ops.append(("1q", snake_position(r, c, cols), u))
         pat = pattern[cyc % len(pattern)]
         for (a, b) in grid_pattern(rows, cols, pat):
             pa = snake_position(a[0], a[1], cols)
