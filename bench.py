@@ -188,29 +188,37 @@ def ours(args):
     achieved = panel["alg_bytes"] / (panel["ms"] * 1e-3) / 1e9 if panel["ms"] > 0 else 0.0
     m.close()
 
-    # --- FP64 path on the same steps
-    m64 = MPS(n, chi, precision="fp64", policy="canon", stream=sptr, device=local)
-    m64.set_sites(sites, centre=i)
-    ms64, st64 = time_steps_at(m64, seq, args.fp64_warmup, args.fp64_steps, torch, stream, i)
-    ms_step64 = ms64 / args.fp64_steps
+    ms_step64 = f64 = fmx = dev_f = dev_o = None
+    if args.fp64_steps > 0:
+        # --- FP64 path on the same steps
+        m64 = MPS(n, chi, precision="fp64", policy="canon", stream=sptr, device=local)
+        m64.set_sites(sites, centre=i)
+        ms64, st64 = time_steps_at(m64, seq, args.fp64_warmup, args.fp64_steps, torch, stream, i)
+        ms_step64 = ms64 / args.fp64_steps
 
-    # --- fidelity deviation: a mixed state run through exactly the FP64 steps
-    mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
-    mm.set_sites([s.astype(np.complex64) for s in sites], centre=i)
-    for stp in seq[:args.fp64_warmup + args.fp64_steps]:
-        do_step_at(mm, stp, i)
-    f64 = m64.fidelity()
-    fmx = mm.fidelity()
-    dev_f = abs(fmx - f64) / f64
-    dev_o = None
-    if not args.skip_overlap:
+        # --- fidelity deviation: a mixed state run through exactly the FP64 steps
+        mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
+        mm.set_sites([s.astype(np.complex64) for s in sites], centre=i)
+        for stp in seq[:args.fp64_warmup + args.fp64_steps]:
+            do_step_at(mm, stp, i)
+        f64 = m64.fidelity()
+        fmx = mm.fidelity()
+        dev_f = abs(fmx - f64) / f64
+    if args.fp64_steps > 0 and not args.skip_overlap:
+        # state-fidelity deviation 1 - |<mix|fp64>|^2 / (<mix|mix> <fp64|fp64>), all by
+        # full FP64 transfer-matrix contraction
         o = mm.overlap(m64)
-        dev_o = 1.0 - abs(o) ** 2 / (fmx * f64)
-    mm.close()
-    m64.close()
+        nmx = mm.overlap(mm).real
+        n64 = m64.overlap(m64).real
+        dev_o = 1.0 - abs(o) ** 2 / (nmx * n64)
+    if args.fp64_steps > 0:
+        mm.close()
+        m64.close()
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed
-    e2e = e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np)
+    e2e = {"value": None, "seconds": 1.0, "steps": 0, "h2d": 0, "d2h": 0}
+    if args.e2e_steps > 0:
+        e2e = e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np)
 
     steps_all = args.steps * ws
     t_max = ms
@@ -221,7 +229,7 @@ def ours(args):
         t = torch.tensor([ms, e2e["seconds"]], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max, e2e_s = float(t[0]), float(t[1])
-        e2e_v = e2e["steps"] * ws / e2e_s
+        e2e_v = e2e["steps"] * ws / e2e_s if e2e["steps"] else None
     value = steps_all / (t_max * 1e-3)
     if rank != 0:
         if ws > 1:
@@ -249,9 +257,10 @@ def ours(args):
             "l2": "inputs larger than L2 (theta %d MiB)" % (((2 * chi) ** 2 * 8) >> 20),
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
-        "fp64_path": {"value": ws * 1e3 / ms_step64, "unit": "applies/s", "ms_per_step": ms_step64,
-                      "steps": args.fp64_steps, "warmup": args.fp64_warmup, "dtype": "c128"},
-        "speedup_vs_fp64": ms_step64 / ms_step,
+        "fp64_path": {"value": ws * 1e3 / ms_step64 if ms_step64 else None, "unit": "applies/s",
+                      "ms_per_step": ms_step64, "steps": args.fp64_steps, "warmup": args.fp64_warmup,
+                      "dtype": "c128"},
+        "speedup_vs_fp64": ms_step64 / ms_step if ms_step64 else None,
         "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o,
                          "steps": args.fp64_warmup + args.fp64_steps, "f_fp64": f64, "f_mixed": fmx},
         "roofline": {"bound": "hbm", "kernel": "qr_panel_kernel (pivoted-QR panel: per-step trailing GEMV)",
@@ -293,33 +302,31 @@ def time_steps_at(m, seq, warmup, steps, torch, stream, i):
 
 
 def e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np):
-    """Each step: the two sites come from pinned host memory, the step runs, the two
-    new sites go back to pinned host memory, all through the C ABI."""
+    """End to end through the C ABI with the two working sites held in pinned host
+    memory: every step uploads them (the state left by the previous step, centre
+    on site i+1), runs the same step as the device-timed loop (1q gates, centre
+    move, gate or SWAP, split) and reads the two new sites back."""
     from paper_2505_06119_gb300 import MPS
 
     m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
     m.set_sites([s.astype(np.complex64) for s in sites], centre=i)
-    a_h = torch.from_numpy(sites[i].astype(np.complex64)).pin_memory()
-    b_h = torch.from_numpy(sites[i + 1].astype(np.complex64)).pin_memory()
-    a_out = torch.empty_like(a_h).pin_memory()
-    b_out = torch.empty_like(b_h).pin_memory()
-    an, bn, ao, bo = a_h.numpy(), b_h.numpy(), a_out.numpy(), b_out.numpy()
+    do_step(m, seq[0], i)
+    shape_a = (chi, 2, chi)
+    a_h = torch.empty(shape_a, dtype=torch.complex64).pin_memory()
+    b_h = torch.empty(shape_a, dtype=torch.complex64).pin_memory()
+    an, bn = a_h.numpy(), b_h.numpy()
+    m.get_site(i, fmt="c64", out=an)
+    m.get_site(i + 1, fmt="c64", out=bn)
     steps = max(1, args.e2e_steps)
-    for st in seq[:1]:
-        m.set_site(i, an)
-        m.set_site(i + 1, bn)
-        m.set_centre(i)
-        do_step(m, st, i)
-        m.get_site(i, fmt="c64")
     m.sync()
     t0 = time.perf_counter()
     for st in seq[1:1 + steps]:
         m.set_site(i, an)
         m.set_site(i + 1, bn)
-        m.set_centre(i)
+        m.set_centre(i + 1)
         do_step(m, st, i)
-        ao[...] = m.get_site(i, fmt="c64")
-        bo[...] = m.get_site(i + 1, fmt="c64")
+        m.get_site(i, fmt="c64", out=an)
+        m.get_site(i + 1, fmt="c64", out=bn)
     m.sync()
     dt = time.perf_counter() - t0
     m.close()

@@ -95,7 +95,7 @@ typedef struct {
   int policy;             /* MPS_POLICY_CANON (default) or MPS_POLICY_LOCAL */
   int device;             /* CUDA device ordinal; default 0 */
   void* stream;           /* cudaStream_t to run on; NULL = the library creates one */
-  int panel_width;        /* QR panel width nb in [1, 64]; 0 = default (32) */
+  int panel_width;        /* QR panel width nb in [1, 32]; 0 = default (32) */
   double wait_timeout_s;  /* limit of every device-side wait; 0 = default (10 s) */
   mps_alloc_fn alloc;     /* optional device allocator; NULL = cudaMalloc */
   mps_free_fn free;       /* must be given together with alloc */
@@ -197,8 +197,9 @@ const char* mps_last_error(mps_t h);
 #define MPS_KCLASS_NORMS 3  /* column-norm recompute */
 #define MPS_KCLASS_FORMQ 4  /* Q formation */
 #define MPS_KCLASS_SPLIT 5  /* site split / reshape / un-pivot */
-#define MPS_KCLASS_OTHER 6  /* 1q gates, centre moves' glue, conversions */
-#define MPS_KCLASS_COUNT 7
+#define MPS_KCLASS_OTHER 6  /* 1q gates, conversions, observables */
+#define MPS_KCLASS_CANON 7  /* centre moves: plain QR / LQ, Q formation, absorption */
+#define MPS_KCLASS_COUNT 8
 
 typedef struct {
   long long launches;   /* kernel launches of this class since the last reset */

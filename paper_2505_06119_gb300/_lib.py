@@ -26,7 +26,7 @@ MPS_HOST_C128 = 0
 MPS_HOST_C64 = 1
 MPS_FLAG_PROFILE = 1
 
-KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other"]
+KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other", "canon"]
 
 ERROR_NAMES = {0: "MPS_OK", -1: "MPS_E_ARG", -2: "MPS_E_NOMEM", -3: "MPS_E_CUDA",
                -4: "MPS_E_TIMEOUT", -5: "MPS_E_STATE", -6: "MPS_E_UNSUPPORTED"}
@@ -53,7 +53,7 @@ class mps_kstat(ctypes.Structure):
                 ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double)]
 
 
-KCLASS_COUNT = 7
+KCLASS_COUNT = 8
 
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p

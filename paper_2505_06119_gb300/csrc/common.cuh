@@ -124,7 +124,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, i
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
     unsigned gen = ld_acquire_u32(&bar[1]);
     unsigned arrived = atom_add_acqrel_u32(&bar[0], 1u);
     if (arrived == expected - 1) {
@@ -145,7 +144,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, i
         }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

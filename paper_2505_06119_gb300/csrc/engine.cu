@@ -21,7 +21,7 @@ using namespace mpsg;
 namespace {
 
 constexpr int kDefaultNb = 32;
-constexpr int kMaxNb = 64;
+constexpr int kMaxNb = 32;
 constexpr int kMaxCoop = 1024;
 constexpr int kNormParts = 256;
 constexpr size_t kAlign = 256;
@@ -39,7 +39,7 @@ int max_bond(int n, int b, int chi) {
 // ---------------------------------------------------------------------------
 // workspace of one two-site split (either precision); carved from one buffer
 struct WsLayout {
-  size_t W, Q, F, vn1, vn2, jpvt, inv, tau, Tfac, Y, Z, red_norm, red_w, red_argv, red_argi, alpha,
+  size_t W, Q, F, vn1, vn2, jpvt, inv, tau, Tfac, Wg, Y, Z, SK, red_norm, red_w, red_argv, red_argi, alpha,
       bar, err, disc, total;
 };
 
@@ -64,8 +64,10 @@ WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int6
   L.inv = take(4 * (size_t)std::max(nmax, 1));
   L.tau = take(esz * (size_t)std::max(kmax, 1));
   L.Tfac = take(esz * (size_t)std::max(npan, 1) * nb * nb);
+  L.Wg = take(16 * (size_t)std::max(npan, 1) * nb * nb);
   L.Y = take(esz * (size_t)nb * std::max(wide, 1));
   L.Z = take(esz * (size_t)nb * std::max(wide, 1));
+  L.SK = take(esz * (size_t)kMaxSplit * nb * std::max(wide, 1));
   L.red_norm = take(8 * (size_t)G);
   L.red_w = take(16 * (size_t)G * nb);
   L.red_argv = take(8 * (size_t)G);
@@ -91,8 +93,10 @@ struct Ws {
   int* inv;
   T* tau;
   T* Tfac;
+  c128* Wg;
   T* Y;
   T* Z;
+  T* SK;
   double* red_norm;
   c128* red_w;
   double* red_argv;
@@ -117,8 +121,10 @@ Ws<T> ws_views(char* base, const WsLayout& L, int64_t ldw, int64_t ldq) {
   w.inv = (int*)(base + L.inv);
   w.tau = (T*)(base + L.tau);
   w.Tfac = (T*)(base + L.Tfac);
+  w.Wg = (c128*)(base + L.Wg);
   w.Y = (T*)(base + L.Y);
   w.Z = (T*)(base + L.Z);
+  w.SK = (T*)(base + L.SK);
   w.red_norm = (double*)(base + L.red_norm);
   w.red_w = (c128*)(base + L.red_w);
   w.red_argv = (double*)(base + L.red_argv);
@@ -152,6 +158,7 @@ QrPlan<T> make_plan(const Ws<T>& w, const Knobs& kn, int m, int n, int k, int pi
   p.tau = w.tau;
   p.jpvt = w.jpvt;
   p.Tfac = w.Tfac;
+  p.Wg = w.Wg;
   p.F = w.F;
   p.vn1 = w.vn1;
   p.vn2 = w.vn2;
@@ -166,6 +173,7 @@ QrPlan<T> make_plan(const Ws<T>& w, const Knobs& kn, int m, int n, int k, int pi
   p.disc_total = disc_total;
   p.Y = w.Y;
   p.Z = w.Z;
+  p.SK = w.SK;
   p.G = kn.G;
   p.flag_tol = kn.flag_tol;
   p.timeout_ns = kn.timeout_ns;
@@ -398,15 +406,16 @@ int move_right(mps_t h, int j) {
   T* sn = (T*)h->site[j + 1];
   cudaStream_t s = h->stream;
   LaunchHooks* hk = &h->prof.hooks;
-  hook_before(hk, MPS_KCLASS_OTHER, 2.0 * m * n * sizeof(T), 0);
+  hook_before(hk, MPS_KCLASS_CANON, 2.0 * m * n * sizeof(T), 0);
   CUTRY(h, transpose_copy<T>(sj, n, w.W, w.ldw, m, n, 0, s), "move_right copy");
-  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  hook_after(hk, MPS_KCLASS_CANON, 1);
   QrPlan<T> p = make_plan<T>(w, h->kn, m, n, k, 0, nullptr, nullptr);
+  p.kclass = MPS_KCLASS_CANON;
   CUTRY(h, qr_factor<T>(p, s, hk), "move_right qr");
   CUTRY(h, qr_form_q<T>(p, w.Q, w.ldq, s, hk), "move_right form_q");
-  hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * m * k * sizeof(T), 0);
+  hook_before(hk, MPS_KCLASS_CANON, 2.0 * m * k * sizeof(T), 0);
   CUTRY(h, transpose_copy<T>(w.Q, w.ldq, sj, k, k, m, 0, s), "move_right split");
-  hook_after(hk, MPS_KCLASS_SPLIT, 1);
+  hook_after(hk, MPS_KCLASS_CANON, 1);
   // next site (k x 2cn) = R (k x cr, upper) * site_{j+1} (cr x 2cn); computed transposed into Q
   GemmDesc<T> d;
   d.M = 2 * cn;
@@ -426,10 +435,10 @@ int move_right(mps_t h, int j) {
   d.b_mask = MASK_UPPER;
   d.C = w.Q;
   d.ldc = 2 * cn;
-  hook_before(hk, MPS_KCLASS_OTHER, ((double)2 * cn * cr + (double)k * cr + 2.0 * cn * k) * sizeof(T),
+  hook_before(hk, MPS_KCLASS_CANON, ((double)2 * cn * cr + (double)k * cr + 2.0 * cn * k) * sizeof(T),
               8.0 * 2 * cn * k * cr);
   CUTRY(h, gemm_simt<T>(d, s), "move_right absorb");
-  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  hook_after(hk, MPS_KCLASS_CANON, 1);
   CUTRY(h, cudaMemcpyAsync(sn, w.Q, sizeof(T) * (size_t)k * 2 * cn, cudaMemcpyDeviceToDevice, s), "move_right copy");
   h->bond[j + 1] = k;
   return MPS_OK;
@@ -446,16 +455,17 @@ int move_left(mps_t h, int j) {
   cudaStream_t s = h->stream;
   LaunchHooks* hk = &h->prof.hooks;
   // W (column-major 2cr x cl) = M^H, M = site j as cl x 2cr row-major
-  hook_before(hk, MPS_KCLASS_OTHER, 2.0 * m * n * sizeof(T), 0);
+  hook_before(hk, MPS_KCLASS_CANON, 2.0 * m * n * sizeof(T), 0);
   CUTRY(h, copy2d<T>(sj, m, w.W, w.ldw, cl, m, 1, s), "move_left copy");
-  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  hook_after(hk, MPS_KCLASS_CANON, 1);
   QrPlan<T> p = make_plan<T>(w, h->kn, m, n, k, 0, nullptr, nullptr);
+  p.kclass = MPS_KCLASS_CANON;
   CUTRY(h, qr_factor<T>(p, s, hk), "move_left qr");
   CUTRY(h, qr_form_q<T>(p, w.Q, w.ldq, s, hk), "move_left form_q");
   // site j (k x 2cr row-major) = Q^H
-  hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * m * k * sizeof(T), 0);
+  hook_before(hk, MPS_KCLASS_CANON, 2.0 * m * k * sizeof(T), 0);
   CUTRY(h, copy2d<T>(w.Q, w.ldq, sj, m, k, m, 1, s), "move_left split");
-  hook_after(hk, MPS_KCLASS_SPLIT, 1);
+  hook_after(hk, MPS_KCLASS_CANON, 1);
   // previous site (2cp x k) = site_{j-1} (2cp x cl) * R^H; transposed: conj(R) (k x cl) * site^T
   GemmDesc<T> d;
   d.M = k;
@@ -475,10 +485,10 @@ int move_left(mps_t h, int j) {
   d.b_mask = MASK_NONE;
   d.C = w.Q;
   d.ldc = k;
-  hook_before(hk, MPS_KCLASS_OTHER, ((double)2 * cp * cl + (double)k * cl + 2.0 * cp * k) * sizeof(T),
+  hook_before(hk, MPS_KCLASS_CANON, ((double)2 * cp * cl + (double)k * cl + 2.0 * cp * k) * sizeof(T),
               8.0 * 2 * cp * k * cl);
   CUTRY(h, gemm_simt<T>(d, s), "move_left absorb");
-  hook_after(hk, MPS_KCLASS_OTHER, 1);
+  hook_after(hk, MPS_KCLASS_CANON, 1);
   CUTRY(h, cudaMemcpyAsync(sp, w.Q, sizeof(T) * (size_t)k * 2 * cp, cudaMemcpyDeviceToDevice, s), "move_left copy");
   h->bond[j] = k;
   return MPS_OK;

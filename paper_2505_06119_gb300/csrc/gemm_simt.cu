@@ -2,6 +2,8 @@
 // complex64): the generic GEMM used by the block-reflector updates, centre
 // moves and contractions, and the theta contraction with its fused gate
 // epilogue (Sec. III-B.1 bond contraction, Sec. III-C.2 tensor application).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace mpsg {
@@ -11,9 +13,9 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
 
 template <typename T>
-__device__ __forceinline__ T load_a(const GemmDesc<T>& d, int i, int k) {
+__device__ __forceinline__ T load_a(const GemmDesc<T>& d, int i, int k, int kend) {
   using R = typename real_of<T>::type;
-  if (i >= d.M || k >= d.K) return mk<R>(0, 0);
+  if (i >= d.M || k >= kend) return mk<R>(0, 0);
   int r = d.a_row ? k : i, c = d.a_row ? i : k;
   if (d.a_mask == MASK_UNIT_LOWER) {
     if (r < c) return mk<R>(0, 0);
@@ -26,9 +28,9 @@ __device__ __forceinline__ T load_a(const GemmDesc<T>& d, int i, int k) {
 }
 
 template <typename T>
-__device__ __forceinline__ T load_b(const GemmDesc<T>& d, int k, int j) {
+__device__ __forceinline__ T load_b(const GemmDesc<T>& d, int k, int j, int kend) {
   using R = typename real_of<T>::type;
-  if (k >= d.K || j >= d.N) return mk<R>(0, 0);
+  if (k >= kend || j >= d.N) return mk<R>(0, 0);
   int r = d.b_row ? j : k, c = d.b_row ? k : j;
   if (d.b_mask == MASK_UNIT_LOWER) {
     if (r < c) return mk<R>(0, 0);
@@ -51,6 +53,13 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmDesc<T> d) {
   __shared__ T Bs[2][BK][BN];
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+  // split-K: this CTA covers K-slice blockIdx.z (whole multiples of BK)
+  int kbeg = 0, kend = d.K;
+  if (d.splitk > 1) {
+    int per = ((d.K + d.splitk - 1) / d.splitk + BK - 1) / BK * BK;
+    kbeg = blockIdx.z * per;
+    kend = min(d.K, kbeg + per);
+  }
   const int tm = tid % 16, tn = tid / 16;
 
   // global->smem mapping (2 elements of A and 2 of B per thread per slice)
@@ -80,10 +89,10 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmDesc<T> d) {
     for (int b = 0; b < 4; ++b) acc[a][b] = mk<R>(0, 0);
 
   T ra[2], rb[2];
-  const int nslices = (d.K + BK - 1) / BK;
+  const int nslices = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
   for (int e = 0; e < 2; ++e) {
-    ra[e] = load_a(d, i0 + ai[e], ak[e]);
-    rb[e] = load_b(d, bk[e], j0 + bj[e]);
+    ra[e] = load_a(d, i0 + ai[e], kbeg + ak[e], kend);
+    rb[e] = load_b(d, kbeg + bk[e], j0 + bj[e], kend);
   }
   for (int e = 0; e < 2; ++e) {
     As[0][ak[e]][ai[e]] = ra[e];
@@ -93,10 +102,10 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmDesc<T> d) {
   for (int s = 0; s < nslices; ++s) {
     const int buf = s & 1;
     if (s + 1 < nslices) {
-      const int kb = (s + 1) * BK;
+      const int kb = kbeg + (s + 1) * BK;
       for (int e = 0; e < 2; ++e) {
-        ra[e] = load_a(d, i0 + ai[e], kb + ak[e]);
-        rb[e] = load_b(d, kb + bk[e], j0 + bj[e]);
+        ra[e] = load_a(d, i0 + ai[e], kb + ak[e], kend);
+        rb[e] = load_b(d, kb + bk[e], j0 + bj[e], kend);
       }
     }
 #pragma unroll
@@ -119,6 +128,20 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmDesc<T> d) {
     }
     __syncthreads();
   }
+  if (d.splitk > 1) {
+    T* P = d.wk + (int64_t)blockIdx.z * d.M * d.N;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int j = j0 + tn * 4 + b;
+      if (j >= d.N) continue;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        int i = i0 + tm * 4 + a;
+        if (i < d.M) P[i + (int64_t)j * d.M] = acc[a][b];
+      }
+    }
+    return;
+  }
   const bool beta_zero = (d.beta.re == (R)0 && d.beta.im == (R)0);
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -134,6 +157,22 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmDesc<T> d) {
       *c = v;
     }
   }
+}
+
+// C = alpha * sum_z P[z] + beta * C, summed in z order
+template <typename T>
+__global__ void splitk_reduce_kernel(GemmDesc<T> d) {
+  using R = typename real_of<T>::type;
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)d.M * d.N;
+  if (idx >= total) return;
+  int64_t i = idx % d.M, j = idx / d.M;
+  T acc = d.wk[idx];
+  for (int z = 1; z < d.splitk; ++z) acc = acc + d.wk[(int64_t)z * total + idx];
+  T* c = d.C + i + j * d.ldc;
+  T v = d.alpha * acc;
+  if (!(d.beta.re == (R)0 && d.beta.im == (R)0)) v = v + d.beta * (*c);
+  *c = v;
 }
 
 // theta tile: 32 values of l (64 rows of A) x 32 values of r (both halves d=0,1).
@@ -264,12 +303,27 @@ __global__ void __launch_bounds__(NT) theta_kernel(ThetaArgs<T> p) {
 
 }  // namespace
 
+int choose_splitk(int M, int N, int K, int max_split) {
+  int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  int want = (2 * 152 + tiles - 1) / tiles;
+  int by_k = K / 256;
+  int s = std::min(std::min(want, by_k), max_split);
+  return s < 1 ? 1 : s;
+}
+
 template <typename T>
 cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s) {
   if (d.M <= 0 || d.N <= 0) return cudaSuccess;
-  dim3 grid((d.M + BM - 1) / BM, (d.N + BN - 1) / BN);
+  const int sk = (d.splitk > 1 && d.wk) ? d.splitk : 1;
+  dim3 grid((d.M + BM - 1) / BM, (d.N + BN - 1) / BN, sk);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  gemm_simt_kernel<T><<<grid, NT, 0, s>>>(d);
+  GemmDesc<T> dd = d;
+  dd.splitk = sk;
+  gemm_simt_kernel<T><<<grid, NT, 0, s>>>(dd);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || sk == 1) return e;
+  int64_t total = (int64_t)d.M * d.N;
+  splitk_reduce_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dd);
   return cudaGetLastError();
 }
 

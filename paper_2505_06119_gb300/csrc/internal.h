@@ -20,23 +20,35 @@ namespace mpsg {
 //     MASK_UNIT_LOWER: r > c -> stored, r == c -> 1, r < c -> 0  (reflectors V)
 //     MASK_UPPER:      r <= c -> stored, else 0                   (R factor)
 enum { MASK_NONE = 0, MASK_UNIT_LOWER = 1, MASK_UPPER = 2 };
+constexpr int kMaxSplit = 8;
 
 template <typename T>
 struct GemmDesc {
-  int M, N, K;
-  T alpha, beta;
-  const T* A;
-  int64_t lda;
-  int a_row, a_conj, a_mask;
-  const T* B;
-  int64_t ldb;
-  int b_row, b_conj, b_mask;
-  T* C;
-  int64_t ldc;
+  int M = 0, N = 0, K = 0;
+  T alpha{}, beta{};
+  const T* A = nullptr;
+  int64_t lda = 0;
+  int a_row = 0, a_conj = 0, a_mask = MASK_NONE;
+  const T* B = nullptr;
+  int64_t ldb = 0;
+  int b_row = 0, b_conj = 0, b_mask = MASK_NONE;
+  T* C = nullptr;
+  int64_t ldc = 0;
+  // split-K: with splitk > 1 the K range is cut into splitk slices whose
+  // products land in wk (splitk * M * N elements) and are summed in a fixed order.
+  int splitk = 0;
+  T* wk = nullptr;
 };
 
 template <typename T>
 cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s);
+// number of kernel launches gemm_simt makes for this descriptor
+template <typename T>
+int gemm_launches(const GemmDesc<T>& d) {
+  return d.splitk > 1 ? 2 : 1;
+}
+// split count that fills the GPU for a skinny product (few output tiles, long K)
+int choose_splitk(int M, int N, int K, int max_split);
 
 // theta contraction with the gate epilogue (Sec. III-B.1 + III-C.2):
 //   X[(l,c),(d,r)] = sum_mu A[l,c,mu] B[mu,d,r]
@@ -91,6 +103,7 @@ struct QrPlan {
   T* tau;          // k
   int* jpvt;       // n
   T* Tfac;         // ceil(k/nb) * nb * nb, per-panel triangular factors (column-major nb x nb)
+  c128* Wg;        // ceil(k/nb) * nb * nb, per-step w = V^H v saved by the panel kernel
   T* F;            // n x nb row-major (ld nb)
   double* vn1;     // n
   double* vn2;     // n
@@ -106,10 +119,12 @@ struct QrPlan {
   double* disc_total; // optional: discarded is also added here
   T* Y;               // nb * max(n, k) scratch for block-reflector GEMMs
   T* Z;               // nb * max(n, k)
+  T* SK;              // split-K partials: kMaxSplit * nb * max(n, k)
   int G;              // cooperative grid size cap
   double flag_tol;    // norm-downdate recompute threshold
   unsigned long long timeout_ns;
   unsigned barrier_extra;  // 0 normally; >0 only to exercise the timeout path
+  int kclass = -1;         // >= 0: attribute every launch to this kernel class
 };
 
 struct LaunchHooks;  // profiling hooks (engine.cu)

@@ -6,8 +6,8 @@
 //
 //   panel kernel (persistent, cooperative, one CTA per SM at most), for each
 //   step J of the panel:
-//     A. pivot p = argmax_t vn1[t] over trailing columns (FP64, lowest index
-//        on ties), from per-CTA partial maxima;
+//     A. pivot p = argmax_t vn1[t] over trailing columns (vn1 = squared column
+//        norms in FP64; lowest index on ties), from per-CTA partial maxima;
 //     B. swap columns J and p; bring column J up to date with the panel's
 //        earlier reflectors, x = W[J:m, J] - V F[p,:]^H; partial sums of
 //        ||x_{J+1:}||^2 (FP64) and V^H x;
@@ -17,8 +17,11 @@
 //        y_t = W[J:m, t]^H v (the BLAS-2 sweep over the trailing matrix),
 //        F[t, k] = tau (y_t - F[t, :k] w) with w = V^H v,
 //        row update W[J, t] -= W[J, panel] F[t, :]^H (this row is final R),
-//        FP64 norm downdate of vn1[t] with an exact recompute when the
-//        downdate loses accuracy (|vn1|/|vn2| below a threshold).
+//        FP64 downdate of the squared norm, vn1[t] -= |W[J, t]|^2, with an
+//        exact recompute when vn1[t] <= tol * vn2[t] (vn2 = the last exact
+//        value), the accuracy criterion of LAPACK's xLAQPS.
+//   The data path (F, the row update, V^H v) runs in the data precision;
+//   FP64 carries the norms, the reflector norm / beta / tau and the pivots.
 //   Two grid barriers per step, every wait bounded.
 //
 //   trailing update: W[J1:m, J1:n] -= V F^H (rank-nb GEMM), then an exact FP64
@@ -41,6 +44,9 @@ namespace {
 
 constexpr int PNT = 512;  // threads of the panel kernel
 constexpr int PNW = PNT / 32;
+constexpr int kPanelNbMax = 32;  // widest panel the kernel supports
+constexpr int kDBatch = 32;      // trailing columns per phase-D batch
+constexpr int kDChMax = 32;      // row chunks per column in phase D (about 8 KB each)
 
 template <typename T>
 struct PanelArgs {
@@ -49,16 +55,16 @@ struct PanelArgs {
   int m, n;
   int j0, kb, nend, nb;
   int pivot;
-  int gb;  // CTAs taking part in phase B
   T* F;
-  double* vn1;
-  double* vn2;
+  double* vn1;  // squared column norms (current)
+  double* vn2;  // squared column norms at the last exact computation
   int* jpvt;
   T* tau;
   T* Tp;  // this panel's T factor, column-major nb x nb
+  c128* Wg;  // this panel's w vectors, nb x nb (column kk = w of step kk)
   double* red_norm;
-  c128* red_w;
-  double* red_argv;
+  T* red_w;
+  long long* red_argv;
   int* red_argi;
   c128* alpha_slot;
   unsigned* bar;
@@ -69,16 +75,24 @@ struct PanelArgs {
   int xcap;  // elements of x that fit in dynamic shared memory
 };
 
-__device__ __forceinline__ bool better(double v, int i, double bv, int bi) {
+// Pivot key of a squared norm: for a non-negative double (or +inf) its bit
+// pattern orders like its value, so pivots are compared as 64-bit integers
+// (exact, and off the FP64 pipe); NaN or negative values map to -1 and never win.
+__device__ __forceinline__ long long pkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return (b >= 0 && b <= 0x7FF0000000000000LL) ? b : -1LL;
+}
+
+__device__ __forceinline__ bool better(long long v, int i, long long bv, int bi) {
   return (v > bv) || (v == bv && i < bi);
 }
 
-// Block-wide argmax of (value, index) pairs; result valid in thread 0.
-__device__ void block_argmax(double& v, int& i) {
-  __shared__ double sv[PNW];
+// Block-wide argmax of (key, index) pairs; result valid in thread 0.
+__device__ void block_argmax(long long& v, int& i) {
+  __shared__ long long sv[PNW];
   __shared__ int si[PNW];
   for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    long long ov = __shfl_xor_sync(0xffffffffu, v, o);
     int oi = __shfl_xor_sync(0xffffffffu, i, o);
     if (better(ov, oi, v, i)) {
       v = ov;
@@ -124,21 +138,128 @@ __device__ __forceinline__ void split_range(int lo, int hi, int parts, int idx, 
   b = lo + (int)((int64_t)len * (idx + 1) / parts);
 }
 
+// Dot product sum_{r in [r0, r1)} conj(col[r]) * xb[r - base] by one warp
+// (base even, xb 16-byte aligned), 16-byte vector loads of the column and of
+// x, eight column loads in flight per lane.
+template <typename T>
+__device__ __forceinline__ T warp_dot_conj(const T* __restrict__ col, const T* __restrict__ xb, int base, int r0,
+                                           int r1, int lane);
+
+__device__ __forceinline__ void dot_pair(float4 v, float4 x, float& ar, float& ai, float& br, float& bi) {
+  // (v.x + i v.y)^* (x.x + i x.y) and (v.z + i v.w)^* (x.z + i x.w)
+  ar = fmaf(v.x, x.x, ar);
+  ar = fmaf(v.y, x.y, ar);
+  ai = fmaf(v.x, x.y, ai);
+  ai = fmaf(-v.y, x.x, ai);
+  br = fmaf(v.z, x.z, br);
+  br = fmaf(v.w, x.w, br);
+  bi = fmaf(v.z, x.w, bi);
+  bi = fmaf(-v.w, x.z, bi);
+}
+
+template <>
+__device__ __forceinline__ c64 warp_dot_conj<c64>(const c64* __restrict__ col, const c64* __restrict__ xb, int base,
+                                                  int r0, int r1, int lane) {
+  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+  // an odd first row (the only possible one: chunks end on even rows, m is even)
+  // is taken by lane 0; its load is issued now and consumed after the sweep
+  const bool peel = (r0 & 1) && r0 < r1;
+  const int r = peel ? r0 + 1 : r0;
+  c64 pc = mk<float>(0.f, 0.f), px = mk<float>(0.f, 0.f);
+  if (peel && lane == 0) {
+    pc = col[r0];
+    px = xb[r0 - base];
+  }
+  const int npairs = (r1 - r) >> 1;
+  const float4* c4 = reinterpret_cast<const float4*>(col + r);
+  const float4* x4 = reinterpret_cast<const float4*>(xb + (r - base));
+  constexpr int UN = 8;
+  // lane-uniform trip count, predicated loads: no lane ever runs a tail alone
+  for (int q0 = 0; q0 < npairs; q0 += 32 * UN) {
+    float4 vv[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const int q = q0 + lane + 32 * u;
+      vv[u] = q < npairs ? c4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const int q = q0 + lane + 32 * u;
+      if (q < npairs) dot_pair(vv[u], x4[q], ar, ai, br, bi);
+    }
+  }
+  if (((r1 - r) & 1) && lane == 0) {  // odd last row: cannot happen with even chunk ends
+    c64 c = col[r1 - 1], v = xb[r1 - 1 - base];
+    br = fmaf(c.re, v.re, br);
+    br = fmaf(c.im, v.im, br);
+    bi = fmaf(c.re, v.im, bi);
+    bi = fmaf(-c.im, v.re, bi);
+  }
+  ar = fmaf(pc.re, px.re, ar);
+  ar = fmaf(pc.im, px.im, ar);
+  ai = fmaf(pc.re, px.im, ai);
+  ai = fmaf(-pc.im, px.re, ai);
+  c64 s;
+  s.re = warp_sum(ar + br);
+  s.im = warp_sum(ai + bi);
+  return s;
+}
+
+template <>
+__device__ __forceinline__ c128 warp_dot_conj<c128>(const c128* __restrict__ col, const c128* __restrict__ xb,
+                                                    int base, int r0, int r1, int lane) {
+  double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+  const double2* c2 = reinterpret_cast<const double2*>(col);
+  const double2* x2 = reinterpret_cast<const double2*>(xb) - base;
+  constexpr int UN = 8;
+  for (int r00 = r0; r00 < r1; r00 += 32 * UN) {
+    double2 vv[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const int r = r00 + lane + 32 * u;
+      vv[u] = r < r1 ? c2[r] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const int r = r00 + lane + 32 * u;
+      if (r < r1) {
+        const double2 xv = x2[r];
+        const double2 v = vv[u];
+        if (u & 1) {
+          br = fma(v.x, xv.x, br);
+          br = fma(v.y, xv.y, br);
+          bi = fma(v.x, xv.y, bi);
+          bi = fma(-v.y, xv.x, bi);
+        } else {
+          ar = fma(v.x, xv.x, ar);
+          ar = fma(v.y, xv.y, ar);
+          ai = fma(v.x, xv.y, ai);
+          ai = fma(-v.y, xv.x, ai);
+        }
+      }
+    }
+  }
+  c128 s;
+  s.re = warp_sum(ar + br);
+  s.im = warp_sum(ai + bi);
+  return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   using R = typename real_of<T>::type;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);
-  __shared__ c128 s_w[64];        // w_i = V_i^H v
-  __shared__ T s_fp[64];          // F[p, :kk] (phase B)
-  __shared__ T s_vrow[64];        // W[J, j0+i], i < kk
-  __shared__ double s_bv;
+  __shared__ T s_w[kPanelNbMax];      // w_i = V_i^H v
+  __shared__ T s_vrow[kPanelNbMax];   // W[J, j0+i]
+  __shared__ T s_wp[PNW][kPanelNbMax];  // per-warp partials of V^H x (phase B)
+  __shared__ T s_dp[kDBatch * kDChMax];  // phase-D chunk sums
   __shared__ int s_bi;
-  __shared__ c128 s_scal[3];  // tau, s, beta
+  __shared__ c128 s_scal[3];  // tau, 1/(alpha-beta), beta
 
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int m = a.m;
+  const int m = a.m, nb = a.nb;
   T* W = a.W;
   const int64_t ldw = a.ldw;
   // an earlier bounded wait expired: the factorisation is void, leave at once
@@ -148,10 +269,10 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   if (a.pivot) {
     int c0, c1;
     split_range(a.j0, a.nend, G, b, c0, c1);
-    double bv = -1.0;
+    long long bv = -1;
     int bi = 0x7fffffff;
     for (int t = c0 + tid; t < c1; t += PNT) {
-      double v = a.vn1[t];
+      long long v = pkey(a.vn1[t]);
       if (better(v, t, bv, bi)) {
         bv = v;
         bi = t;
@@ -166,105 +287,189 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   }
 
   c128 s_prev = mk<double>(0, 0);
-  int rb0, rb1;  // phase-B row range of this CTA
-  if (b < a.gb)
-    split_range(0, m, a.gb, b, rb0, rb1);
-  else
-    rb0 = rb1 = 0;
-
   for (int kk = 0; kk < a.kb; ++kk) {
     const int J = a.j0 + kk;
+    // rows J..m-1 of the phase-B work: at most 128 per CTA
+    const int gb = max(1, min(G, (m - J + 127) / 128));
     // ---------------- A: pivot
     int p = J;
     if (a.pivot) {
-      if (tid < 32) {
-        double bv = -1.0;
+      if (warp == 0) {
+        long long bv = -1;
         int bi = 0x7fffffff;
-        for (int g = lane; g < G; g += 32) {
-          double v = a.red_argv[g];
-          int i = a.red_argi[g];
-          if (better(v, i, bv, bi)) {
-            bv = v;
-            bi = i;
+        long long v[5];
+        int ix[5];
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+          const int g = lane + 32 * u;
+          v[u] = -1;
+          ix[u] = 0x7fffffff;
+          if (g < G) {
+            v[u] = a.red_argv[g];
+            ix[u] = a.red_argi[g];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 5; ++u)
+          if (better(v[u], ix[u], bv, bi)) {
+            bv = v[u];
+            bi = ix[u];
+          }
+        for (int g = lane + 160; g < G; g += 32) {  // more than 160 CTAs
+          long long vv = a.red_argv[g];
+          int ii = a.red_argi[g];
+          if (better(vv, ii, bv, bi)) {
+            bv = vv;
+            bi = ii;
           }
         }
         for (int o = 16; o > 0; o >>= 1) {
-          double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
           int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (better(ov, oi, bv, bi)) {
             bv = ov;
             bi = oi;
           }
         }
-        if (lane == 0) {
-          s_bv = bv;
-          s_bi = bi;
-        }
+        if (lane == 0) s_bi = bi;
       }
       __syncthreads();
       p = s_bi;
-      if (p < J || p >= a.nend) {  // cannot happen with finite norms
+      if (p < J || p >= a.nend) {  // only reachable with non-finite norms
         if (tid == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_NONFINITE);
         p = J;
       }
     }
-    // ---------------- B: swap, column update, partial sums
-    if (b < a.gb) {
-      for (int i = tid; i < kk; i += PNT) s_fp[i] = a.F[(int64_t)p * a.nb + i];
-      __syncthreads();
-      T* colJ = W + (int64_t)J * ldw;
-      T* colP = W + (int64_t)p * ldw;
-      if (kk > 0) {  // deferred scaling of the previous reflector (rows > J-1)
-        T* prev = W + (int64_t)(J - 1) * ldw;
-        T sc = ccast<R>(s_prev);
-        for (int r = max(rb0, J) + tid; r < rb1; r += PNT) prev[r] = prev[r] * sc;
+    T* colJ = W + (int64_t)J * ldw;
+    T* colP = W + (int64_t)p * ldw;
+    // ---------------- B1: swap rows above J (any CTA)
+    if (p != J) {
+      int s0, s1;
+      split_range(0, J, G, b, s0, s1);
+      for (int r = s0 + tid; r < s1; r += PNT) {
+        T t0 = colJ[r];
+        colJ[r] = colP[r];
+        colP[r] = t0;
       }
-      if (p != J)
-        for (int r = rb0 + tid; r < rb1; r += PNT) {
-          T t0 = colJ[r];
-          colJ[r] = colP[r];
-          colP[r] = t0;
+    }
+    // ---------------- B2: rows [u0, u1) of J..m-1: swap, deferred scaling of the
+    // previous reflector, column update x = W[:,J] - V F[p,:]^H, partial sums.
+    // 4 threads per row; thread `sub` owns panel columns i = sub + 4u.
+    if (b < gb) {
+      int u0, u1;
+      split_range(J, m, gb, b, u0, u1);
+      const int sub = tid & 3;
+      const int r = u0 + (tid >> 2);
+      const bool act = r < u1;
+      constexpr int U = kPanelNbMax / 4;
+      T vr[U], fp[U];
+      // issue every load of this phase before using any
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = sub + 4 * u;
+        vr[u] = mk<R>(0, 0);
+        fp[u] = mk<R>(0, 0);
+        if (i < kk) {
+          fp[u] = a.F[(int64_t)p * nb + i];
+          if (act) vr[u] = W[r + (int64_t)(a.j0 + i) * ldw];
         }
-      __syncthreads();
+      }
+      T cj = mk<R>(0, 0), cp = mk<R>(0, 0);
+      if (act && sub == 0) {
+        cj = colJ[r];
+        cp = colP[r];
+      }
+      if (kk > 0 && act && sub == ((kk - 1) & 3)) {  // previous reflector: rows > J-1, scaled once
+        const int u = (kk - 1) >> 2;
+        const T scp = ccast<R>(s_prev);
+#pragma unroll
+        for (int uu = 0; uu < U; ++uu)
+          if (uu == u) {
+            vr[uu] = vr[uu] * scp;
+            W[r + (int64_t)(J - 1) * ldw] = vr[uu];
+          }
+      }
+      T x = (sub == 0) ? ((p != J) ? cp : cj) : mk<R>(0, 0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) x = x - vr[u] * cconj(fp[u]);
+      x.re += __shfl_xor_sync(0xffffffffu, x.re, 1);
+      x.im += __shfl_xor_sync(0xffffffffu, x.im, 1);
+      x.re += __shfl_xor_sync(0xffffffffu, x.re, 2);
+      x.im += __shfl_xor_sync(0xffffffffu, x.im, 2);
       double nrm = 0.0;
-      for (int r = max(rb0, J) + tid; r < rb1; r += PNT) {
-        T x = colJ[r];
-        for (int i = 0; i < kk; ++i) {
-          T v = W[r + (int64_t)(a.j0 + i) * ldw];
-          // x -= v * conj(F[p, i])
-          x = x - v * cconj(s_fp[i]);
-        }
+      if (act && sub == 0) {
         colJ[r] = x;
-        if (r > J) nrm += (double)cabs2(x);
+        if (p != J) colP[r] = cj;
+        if (r > J) nrm = (double)x.re * (double)x.re + (double)x.im * (double)x.im;
         if (r == J) *a.alpha_slot = ccast<double>(x);
       }
-      nrm = block_sum(nrm);
+      // partial w_i = sum_{rows > J} conj(V[r, i]) x_r: reduce over the 8 rows of the warp
+      const bool below = act && r > J;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        T c = mk<R>(0, 0);
+        if (below) c = cconj(vr[u]) * x;
+        c.re += __shfl_xor_sync(0xffffffffu, c.re, 4);
+        c.im += __shfl_xor_sync(0xffffffffu, c.im, 4);
+        c.re += __shfl_xor_sync(0xffffffffu, c.re, 8);
+        c.im += __shfl_xor_sync(0xffffffffu, c.im, 8);
+        c.re += __shfl_xor_sync(0xffffffffu, c.re, 16);
+        c.im += __shfl_xor_sync(0xffffffffu, c.im, 16);
+        if (lane < 4) s_wp[warp][sub + 4 * u] = c;
+      }
+      nrm = block_sum(nrm);  // contains __syncthreads: s_wp complete afterwards
       if (tid == 0) a.red_norm[b] = nrm;
-      __syncthreads();
-      // partial w_i = sum_{r > J} conj(V[r, i]) x_r over this CTA's rows
-      for (int i = warp; i < kk; i += PNW) {
-        c128 acc = mk<double>(0, 0);
-        const T* vc = W + (int64_t)(a.j0 + i) * ldw;
-        for (int r = max(rb0, J + 1) + lane; r < rb1; r += 32) cfma_conj(acc, ccast<double>(vc[r]), ccast<double>(colJ[r]));
-        acc.re = warp_sum(acc.re);
-        acc.im = warp_sum(acc.im);
-        if (lane == 0) a.red_w[(int64_t)b * a.nb + i] = acc;
+      if (tid < kk) {
+        T w = s_wp[0][tid];
+        for (int q = 1; q < PNW; ++q) w = w + s_wp[q][tid];
+        a.red_w[(int64_t)b * nb + tid] = w;
       }
-      if (b == 0 && tid == 0 && p != J) {
-        int t0 = a.jpvt[J];
-        a.jpvt[J] = a.jpvt[p];
-        a.jpvt[p] = t0;
-      }
+    }
+    if (b == 0 && tid == 0 && p != J) {
+      int t0 = a.jpvt[J];
+      a.jpvt[J] = a.jpvt[p];
+      a.jpvt[p] = t0;
     }
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
 
     // ---------------- C: reflector (every CTA, identical FP64 arithmetic)
-    if (tid < 32) {
+    const int L = m - J - 1;  // rows below the pivot row
+    // x = W[J+1:m, J] staged from the even row xbase (16-byte aligned vectors)
+    const int xbase = (sizeof(T) == 8) ? ((J + 1) & ~1) : (J + 1);
+    const bool staged = (m - xbase <= a.xcap);
+    // all loads of this phase first: partial sums, row J of V, x for phase D
+    double nv[5];
+    c128 al = mk<double>(0, 0);
+    if (warp == 0) {
+#pragma unroll
+      for (int u = 0; u < 5; ++u) {
+        const int g = lane + 32 * u;
+        nv[u] = g < gb ? a.red_norm[g] : 0.0;
+      }
+      if (lane == 0) al = *a.alpha_slot;
+    }
+    T wv[2][5];
+    T vrw[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = warp + PNW * q;
+      vrw[q] = mk<R>(0, 0);
+#pragma unroll
+      for (int u = 0; u < 5; ++u) {
+        const int g = lane + 32 * u;
+        wv[q][u] = (i < kk && g < gb) ? a.red_w[(int64_t)g * nb + i] : mk<R>(0, 0);
+      }
+      if (i < kk && lane == 0) vrw[q] = W[J + (int64_t)(a.j0 + i) * ldw];
+    }
+    if (staged)
+      for (int r = tid; r < m - xbase; r += PNT) xs[r] = colJ[xbase + r];
+    if (warp == 0) {
       double xn = 0.0;
-      if (lane == 0)
-        for (int g = 0; g < a.gb; ++g) xn += a.red_norm[g];
+#pragma unroll
+      for (int u = 0; u < 5; ++u) xn += nv[u];
+      for (int g = lane + 160; g < gb; g += 32) xn += a.red_norm[g];
+      xn = warp_sum(xn);
       if (lane == 0) {
-        c128 al = *a.alpha_slot;
         c128 tau, sc, beta;
         if (xn == 0.0 && al.im == 0.0) {
           tau = mk<double>(0, 0);
@@ -285,130 +490,160 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       }
     }
     __syncthreads();
-    const c128 tau = s_scal[0], sc = s_scal[1];
-    for (int i = warp; i < kk; i += PNW) {
-      c128 acc = mk<double>(0, 0);
-      for (int g = lane; g < a.gb; g += 32) {
-        c128 v = a.red_w[(int64_t)g * a.nb + i];
-        acc.re += v.re;
-        acc.im += v.im;
-      }
-      // fixed-order lane tree: identical in every CTA
+    // tau and 1/(alpha-beta) are FP64 results; the data path uses them rounded
+    const T tau = ccast<R>(s_scal[0]), sc = ccast<R>(s_scal[1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = warp + PNW * q;
+      T acc = mk<R>(0, 0);
+#pragma unroll
+      for (int u = 0; u < 5; ++u) acc = acc + wv[q][u];
+      if (i < kk)
+        for (int g = lane + 160; g < gb; g += 32) acc = acc + a.red_w[(int64_t)g * nb + i];
       acc.re = warp_sum(acc.re);
       acc.im = warp_sum(acc.im);
-      if (lane == 0) {
-        c128 vr = ccast<double>(W[J + (int64_t)(a.j0 + i) * ldw]);
-        s_w[i] = cconj(vr) + sc * acc;  // V_i^H v
+      if (i < kk && lane == 0) {
+        s_vrow[i] = vrw[q];
+        s_w[i] = cconj(vrw[q]) + sc * acc;  // V_i^H v
       }
     }
-    for (int i = tid; i < kk; i += PNT) s_vrow[i] = W[J + (int64_t)(a.j0 + i) * ldw];
     __syncthreads();
-    if (b == 0 && tid == 0) {
-      a.tau[J] = ccast<R>(tau);
-      W[J + (int64_t)J * ldw] = ccast<R>(s_scal[2]);
-      // T[0:kk, kk] = -tau T[0:kk, 0:kk] w ;  T[kk, kk] = tau
-      T* Tc = a.Tp + (int64_t)kk * a.nb;
-      for (int i = 0; i < kk; ++i) {
-        c128 acc = mk<double>(0, 0);
-        for (int j = i; j < kk; ++j) cfma(acc, ccast<double>(a.Tp[i + (int64_t)j * a.nb]), s_w[j]);
-        Tc[i] = ccast<R>(mk<double>(0, 0) - tau * acc);
+    if (b == 0) {
+      // w of this step, for the triangular factor T of the panel (tfactor_kernel)
+      if (tid < kk) a.Wg[(int64_t)kk * nb + tid] = ccast<double>(s_w[tid]);
+      if (tid == 32) {
+        a.tau[J] = tau;
+        W[J + (int64_t)J * ldw] = ccast<R>(s_scal[2]);
       }
-      Tc[kk] = ccast<R>(tau);
     }
 
-    // ---------------- D: trailing columns
-    const int L = m - J - 1;  // rows below the pivot row
-    const bool staged = (L <= a.xcap);
-    const T* colJ = W + (int64_t)J * ldw;
-    if (staged) {
-      for (int r = tid; r < L; r += PNT) xs[r] = colJ[J + 1 + r];
-      __syncthreads();
-    }
+    // ---------------- D: trailing columns in batches of up to kDBatch; each column's
+    // sweep y_t = W[J+1:m, t]^H x is cut into row chunks of about 8 KB so that
+    // the items (column, chunk) spread evenly over the warps; chunk sums are
+    // combined in a fixed order, then one warp per column finishes F, the row
+    // update and the norm downdate.
+    const T* xsrc = staged ? xs : colJ + xbase;
+    // chunks on even absolute rows: [xbase + ch*chr, xbase + (ch+1)*chr) clipped to [J+1, m)
+    const int Lx = m - xbase;
+    const int nch = max(1, min(kDChMax, (int)(((int64_t)Lx * sizeof(T) + 8191) / 8192)));
+    const int chr = (((Lx + nch - 1) / nch) + 1) & ~1;  // rows per chunk (even)
     int c0, c1;
     split_range(J + 1, a.nend, G, b, c0, c1);
-    double bv = -1.0;
+    long long bv = -1;
     int bi = 0x7fffffff;
-    for (int t = c0 + warp; t < c1; t += PNW) {
-      const int src = (t == p) ? J : t;
-      const T* col = W + (int64_t)t * ldw;
-      // y_t = sum_{r > J} conj(W[r,t]) x_r   (accumulated in the data precision)
-      T acc = mk<R>(0, 0);
-      if (staged) {
-        for (int r = lane; r < L; r += 32) cfma_conj(acc, col[J + 1 + r], xs[r]);
-      } else {
-        for (int r = lane; r < L; r += 32) cfma_conj(acc, col[J + 1 + r], colJ[J + 1 + r]);
+    for (int cb = c0; cb < c1; cb += kDBatch) {
+      const int nc = min(kDBatch, c1 - cb);
+      // D1: chunk sums
+      for (int it = warp; it < nc * nch; it += PNW) {
+        const int cl = it / nch, ch = it - cl * nch;
+        const int t = cb + cl;
+        const int r0 = max(J + 1, xbase + ch * chr), r1 = min(m, xbase + (ch + 1) * chr);
+        const T* col = W + (int64_t)t * ldw;
+        T s = mk<R>(0, 0);
+        if (r0 < r1) s = warp_dot_conj<T>(col, xsrc, xbase, r0, r1, lane);
+        if (lane == 0) s_dp[cl * kDChMax + ch] = s;
       }
-      acc.re = warp_sum(acc.re);
-      acc.im = warp_sum(acc.im);
-      c128 wJt = ccast<double>(col[J]);
-      c128 y = cconj(wJt) + sc * ccast<double>(acc);
-      // F[t, kk] = tau * (y - sum_i F[src, i] w_i)
-      c128 fw = mk<double>(0, 0), rowu = mk<double>(0, 0);
-      const T* Fs = a.F + (int64_t)src * a.nb;
-      for (int i = lane; i < kk; i += 32) {
-        c128 fi = ccast<double>(Fs[i]);
-        cfma(fw, fi, s_w[i]);
-        cfma(rowu, ccast<double>(s_vrow[i]), cconj(fi));
-      }
-      fw.re = warp_sum(fw.re);
-      fw.im = warp_sum(fw.im);
-      rowu.re = warp_sum(rowu.re);
-      rowu.im = warp_sum(rowu.im);
-      c128 f = tau * (y - fw);
-      T* Ft = a.F + (int64_t)t * a.nb;
-      if (t == p)
-        for (int i = lane; i < kk; i += 32) Ft[i] = Fs[i];
-      __syncwarp();
-      c128 wnew = wJt - rowu - cconj(f);
-      double v1 = 0.0, v2 = 0.0;
-      int need = 0;
-      if (lane == 0) {
-        Ft[kk] = ccast<R>(f);
-        W[J + (int64_t)t * ldw] = ccast<R>(wnew);
-        if (a.pivot) {
-          v1 = a.vn1[src];
-          v2 = a.vn2[src];
-          if (L <= 0) {
-            v1 = 0.0;
-          } else if (v1 != 0.0) {
-            double tt = sqrt(wnew.re * wnew.re + wnew.im * wnew.im) / v1;
-            tt = fmax(0.0, (1.0 + tt) * (1.0 - tt));
-            double t2 = tt * (v1 / v2) * (v1 / v2);
-            if (t2 <= a.flag_tol)
-              need = 1;
-            else
-              v1 = v1 * sqrt(tt);
+      __syncthreads();
+      // D2: per-column epilogue; operands of all of this warp's columns fetched first
+      constexpr int CPW = kDBatch / PNW;  // columns per warp
+      T wJtT[CPW], fiT[CPW];
+      double v1a[CPW], v2a[CPW];
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        const int cl = warp + PNW * q;
+        wJtT[q] = mk<R>(0, 0);
+        fiT[q] = mk<R>(0, 0);
+        v1a[q] = 0.0;
+        v2a[q] = 0.0;
+        if (cl < nc) {
+          const int t = cb + cl;
+          const int src = (t == p) ? J : t;
+          wJtT[q] = W[J + (int64_t)t * ldw];
+          if (lane < kk) fiT[q] = a.F[(int64_t)src * nb + lane];
+          if (lane == 0 && a.pivot) {
+            v1a[q] = a.vn1[src];
+            v2a[q] = a.vn2[src];
           }
         }
       }
-      need = __shfl_sync(0xffffffffu, need, 0);
-      if (need) {
-        // exact norm of the column after step J: rows > J of
-        // W[:, t] - V[:, 0:kk] F[t, 0:kk]^H - (s x) conj(f)
-        double nr = 0.0;
-        c128 cf = cconj(f);
-        for (int r = J + 1 + lane; r < m; r += 32) {
-          c128 z = ccast<double>(col[r]);
-          for (int i = 0; i < kk; ++i) {
-            c128 vv = ccast<double>(W[r + (int64_t)(a.j0 + i) * ldw]);
-            z = z - vv * cconj(ccast<double>(Fs[i]));
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        const int cl = warp + PNW * q;
+        if (cl >= nc) continue;  // warp-uniform
+        const int t = cb + cl;
+        const int src = (t == p) ? J : t;
+        const T* col = W + (int64_t)t * ldw;
+        const T* Fs = a.F + (int64_t)src * nb;
+        T* Ft = a.F + (int64_t)t * nb;
+        T acc = mk<R>(0, 0);
+        for (int ch = 0; ch < nch; ++ch) acc = acc + s_dp[cl * kDChMax + ch];
+        const T wJt = wJtT[q];
+        const T y = cconj(wJt) + sc * acc;
+        // F[t, kk] = tau * (y - sum_i F[src, i] w_i); row update of W[J, t]
+        T fw = mk<R>(0, 0), rowu = mk<R>(0, 0);
+        if (lane < kk) {
+          const T fi = fiT[q];
+          cfma(fw, fi, s_w[lane]);
+          cfma(rowu, s_vrow[lane], cconj(fi));
+          if (t == p) Ft[lane] = fi;
+        }
+        fw.re = warp_sum(fw.re);
+        fw.im = warp_sum(fw.im);
+        rowu.re = warp_sum(rowu.re);
+        rowu.im = warp_sum(rowu.im);
+        const T f = tau * (y - fw);
+        const T wnew = wJt - rowu - cconj(f);
+        double v1 = v1a[q], v2 = v2a[q];
+        int need = 0;
+        if (lane == 0) {
+          Ft[kk] = f;
+          W[J + (int64_t)t * ldw] = wnew;
+          if (a.pivot) {
+            if (L <= 0) {
+              v1 = 0.0;
+            } else if (v1 > 0.0) {
+              // FP64 downdate of the squared norm; recompute when it has lost accuracy
+              const double r2 = (double)wnew.re * (double)wnew.re + (double)wnew.im * (double)wnew.im;
+              const double c = fmax(v1 - r2, 0.0);
+              if (c <= a.flag_tol * v2)
+                need = 1;
+              else
+                v1 = c;
+            }
           }
-          c128 vx = sc * ccast<double>(colJ[r]);
-          z = z - vx * cf;
-          nr += z.re * z.re + z.im * z.im;
         }
-        nr = warp_sum(nr);
-        v1 = sqrt(nr);
-        v2 = v1;
-      }
-      if (lane == 0 && a.pivot) {
-        a.vn1[t] = v1;
-        a.vn2[t] = v2;
-        if (better(v1, t, bv, bi)) {
-          bv = v1;
-          bi = t;
+        need = __shfl_sync(0xffffffffu, need, 0);
+        if (need) {
+          // exact squared norm of the column after step J: rows > J of
+          // W[:, t] - V[:, 0:kk] F[t, 0:kk]^H - (s x) conj(f)
+          double nr = 0.0;
+          const c128 cf = cconj(ccast<double>(f));
+          const c128 scd = ccast<double>(sc);
+          for (int r = J + 1 + lane; r < m; r += 32) {
+            c128 z = ccast<double>(col[r]);
+            for (int i = 0; i < kk; ++i) {
+              c128 vv = ccast<double>(W[r + (int64_t)(a.j0 + i) * ldw]);
+              z = z - vv * cconj(ccast<double>(Fs[i]));
+            }
+            c128 vx = scd * ccast<double>(colJ[r]);
+            z = z - vx * cf;
+            nr += z.re * z.re + z.im * z.im;
+          }
+          nr = warp_sum(nr);
+          v1 = nr;
+          v2 = nr;
+        }
+        if (lane == 0 && a.pivot) {
+          a.vn1[t] = v1;
+          a.vn2[t] = v2;
+          const long long k1 = pkey(v1);
+          if (better(k1, t, bv, bi)) {
+            bv = k1;
+            bi = t;
+          }
         }
       }
+      __syncthreads();  // s_dp reused by the next batch
     }
     if (a.pivot) {
       block_argmax(bv, bi);
@@ -417,41 +652,129 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         a.red_argi[b] = bi;
       }
     }
-    s_prev = sc;
+    s_prev = s_scal[1];
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
   }
-  // final deferred scaling of the panel's last reflector
-  if (b < a.gb && a.kb > 0) {
+  // final deferred scaling of the panel's last reflector, rows > Jl
+  if (a.kb > 0) {
     const int Jl = a.j0 + a.kb - 1;
+    int u0, u1;
+    split_range(Jl + 1, m, G, b, u0, u1);
     T* prev = W + (int64_t)Jl * ldw;
     T sc = ccast<R>(s_prev);
-    for (int r = max(rb0, Jl + 1) + tid; r < rb1; r += PNT) prev[r] = prev[r] * sc;
+    for (int r = u0 + tid; r < u1; r += PNT) prev[r] = prev[r] * sc;
   }
 }
 
-// vn1[t] = vn2[t] = ||W[r0:m, t]|| for t in [c0, n): one warp per column, FP64.
+// Triangular factor of each panel's block reflector (H_j0 ... H_j0+kb-1 =
+// I - V T V^H, forward columnwise): T[kk, kk] = tau_kk and
+// T[0:kk, kk] = -tau_kk T[0:kk, 0:kk] w_kk with w_kk = V[:, 0:kk]^H v_kk saved by
+// the panel kernel.  One CTA per panel, FP64.
+template <typename T>
+__global__ void tfactor_kernel(const c128* Wg, const T* tau, int pan0, int k, int nb, T* Tfac) {
+  using R = typename real_of<T>::type;
+  __shared__ c128 Ts[kPanelNbMax * kPanelNbMax];
+  const int pan = pan0 + blockIdx.x;
+  const int j0 = pan * nb, kb = min(nb, k - j0);
+  const c128* w = Wg + (size_t)pan * nb * nb;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) Ts[e] = mk<double>(0, 0);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int kk = 0; kk < kb; ++kk) {
+      const c128 t = ccast<double>(tau[j0 + kk]);
+      for (int i = lane; i < kk; i += 32) {
+        c128 acc = mk<double>(0, 0);
+        for (int j = i; j < kk; ++j) cfma(acc, Ts[i + j * nb], w[(size_t)kk * nb + j]);
+        Ts[i + kk * nb] = mk<double>(0, 0) - t * acc;
+      }
+      if (lane == 0) Ts[kk + kk * nb] = t;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  T* out = Tfac + (size_t)pan * nb * nb;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) out[e] = ccast<R>(Ts[e]);
+}
+
+// Squared norm of col[r0:r1) by one warp.  complex128: FP64 throughout.
+// complex64: FP32 squares summed per lane with Kahan compensation (error of
+// order the FP32 unit roundoff, independent of the length), lanes combined in
+// FP64; 16-byte vector loads.
+template <typename T>
+__device__ __forceinline__ double warp_norm2(const T* __restrict__ col, int r0, int r1, int lane);
+
+template <>
+__device__ __forceinline__ double warp_norm2<c64>(const c64* __restrict__ col, int r0, int r1, int lane) {
+  float s = 0.f, c = 0.f;
+  auto add = [&](float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  };
+  int r = r0;
+  if ((r & 1) && r < r1) {
+    if (lane == 0) add(cabs2(col[r]));
+    ++r;
+  }
+  const int npairs = (r1 - r) >> 1;
+  const float4* c4 = reinterpret_cast<const float4*>(col + r);
+  for (int q0 = 0; q0 < npairs; q0 += 256) {
+    float4 vv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = q0 + lane + 32 * u;
+      vv[u] = q < npairs ? c4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) add(vv[u].x * vv[u].x + vv[u].y * vv[u].y + vv[u].z * vv[u].z + vv[u].w * vv[u].w);
+  }
+  if (((r1 - r) & 1) && lane == 0) add(cabs2(col[r1 - 1]));
+  return warp_sum((double)s - (double)c);
+}
+
+template <>
+__device__ __forceinline__ double warp_norm2<c128>(const c128* __restrict__ col, int r0, int r1, int lane) {
+  double a = 0.0, b = 0.0;
+  const double2* c2 = reinterpret_cast<const double2*>(col);
+  for (int r00 = r0; r00 < r1; r00 += 256) {
+    double2 vv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = r00 + lane + 32 * u;
+      vv[u] = r < r1 ? c2[r] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      a = fma(vv[u].x, vv[u].x, a);
+      a = fma(vv[u].y, vv[u].y, a);
+      b = fma(vv[u + 1].x, vv[u + 1].x, b);
+      b = fma(vv[u + 1].y, vv[u + 1].y, b);
+    }
+  }
+  return warp_sum(a + b);
+}
+
+// vn1[t] = vn2[t] = ||W[r0:m, t]||^2 for t in [c0, n): one warp per column.
 template <typename T>
 __global__ void col_norms_kernel(const T* W, int64_t ldw, int m, int r0, int c0, int n, double* vn1,
                                  double* vn2) {
   const int lane = threadIdx.x & 31;
   const int t = c0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (t >= n) return;
-  const T* col = W + (int64_t)t * ldw;
-  double s = 0.0;
-  for (int r = r0 + lane; r < m; r += 32) s += (double)cabs2(col[r]);
-  s = warp_sum(s);
+  double s = warp_norm2<T>(W + (int64_t)t * ldw, r0, m, lane);
   if (lane == 0) {
-    double v = sqrt(s);
-    vn1[t] = v;
-    vn2[t] = v;
+    vn1[t] = s;
+    vn2[t] = s;
   }
 }
 
-// discarded = sum_{t in [c0, n)} vn1[t]^2, one block, fixed order
+// discarded = sum_{t in [c0, n)} vn1[t] (squared norms), one block, fixed order
 __global__ void discarded_kernel(const double* vn1, int c0, int n, double* out, double* total) {
   __shared__ double s[256];
   double acc = 0.0;
-  for (int t = c0 + threadIdx.x; t < n; t += 256) acc += vn1[t] * vn1[t];
+  for (int t = c0 + threadIdx.x; t < n; t += 256) acc += vn1[t];
   s[threadIdx.x] = acc;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -483,16 +806,18 @@ int num_sms() {
   return g_sms;
 }
 
+constexpr int kPanelSmem = 200 * 1024;  // dynamic shared memory of the panel kernel
+
 template <typename T>
-static int panel_xcap() {
-  return (200 * 1024) / (int)sizeof(T);
+static int panel_xcap(int) {
+  return kPanelSmem / (int)sizeof(T);
 }
 
 template <typename T>
 static cudaError_t panel_setup(int& max_blocks) {
   static int cached = -1;
   if (cached < 0) {
-    int smem = panel_xcap<T>() * (int)sizeof(T);
+    int smem = kPanelSmem;
     cudaError_t e = cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -511,14 +836,22 @@ static cudaError_t panel_setup(int& max_blocks) {
     if (e_ != cudaSuccess) return e_;          \
   } while (0)
 
+// Launch accounting of one QR: either by kernel class, or everything under
+// the plan's override class (centre moves).
+struct ClassMap {
+  int over;
+  int operator()(int c) const { return over >= 0 ? over : c; }
+};
+
 template <typename T>
 cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
   using R = typename real_of<T>::type;
+  const ClassMap K{p.kclass};
   const int m = p.m, n = p.n, k = p.k, nb = p.nb;
   if (k <= 0) {
     if (p.pivot && p.discarded) {
       // nothing factored: discarded = ||W||_F^2
-      hook_before(hooks, MPS_KCLASS_NORMS, (double)m * n * sizeof(T), 0);
+      hook_before(hooks, K(MPS_KCLASS_NORMS), (double)m * n * sizeof(T), 0);
       int threads = 256, warps = threads / 32;
       if (n > 0) {
         col_norms_kernel<T><<<(n + warps - 1) / warps, threads, 0, s>>>(p.W, p.ldw, m, 0, 0, n, p.vn1, p.vn2);
@@ -526,7 +859,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       }
       discarded_kernel<<<1, 256, 0, s>>>(p.vn1, 0, n, p.discarded, p.disc_total);
       CK(cudaGetLastError());
-      hook_after(hooks, MPS_KCLASS_NORMS, n > 0 ? 2 : 1);
+      hook_after(hooks, K(MPS_KCLASS_NORMS), n > 0 ? 2 : 1);
     }
     return cudaSuccess;
   }
@@ -535,18 +868,18 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
   const int gcap = std::max(1, std::min(p.G > 0 ? p.G : maxb, maxb));
   const int npanels = (k + nb - 1) / nb;
   CK(cudaMemsetAsync(p.Tfac, 0, sizeof(T) * (size_t)npanels * nb * nb, s));
-  hook_before(hooks, MPS_KCLASS_OTHER, 4.0 * n, 0);
+  hook_before(hooks, K(MPS_KCLASS_OTHER), 4.0 * n, 0);
   iota_kernel<<<(n + 255) / 256, 256, 0, s>>>(p.jpvt, n);
   CK(cudaGetLastError());
-  hook_after(hooks, MPS_KCLASS_OTHER, 1);
+  hook_after(hooks, K(MPS_KCLASS_OTHER), 1);
   if (p.pivot) {
-    hook_before(hooks, MPS_KCLASS_NORMS, (double)m * n * sizeof(T), 3.0 * m * n);
+    hook_before(hooks, K(MPS_KCLASS_NORMS), (double)m * n * sizeof(T), 3.0 * m * n);
     int warps = 8;
     col_norms_kernel<T><<<(n + warps - 1) / warps, warps * 32, 0, s>>>(p.W, p.ldw, m, 0, 0, n, p.vn1, p.vn2);
     CK(cudaGetLastError());
-    hook_after(hooks, MPS_KCLASS_NORMS, 1);
+    hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
   }
-  const int smem = panel_xcap<T>() * (int)sizeof(T);
+  const int smem = kPanelSmem;
   for (int pi = 0; pi < npanels; ++pi) {
     const int j0 = pi * nb;
     const int kb = std::min(nb, k - j0);
@@ -567,19 +900,20 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     a.jpvt = p.jpvt;
     a.tau = p.tau;
     a.Tp = p.Tfac + (size_t)pi * nb * nb;
+    a.Wg = p.Wg + (size_t)pi * nb * nb;
     a.red_norm = p.red_norm;
-    a.red_w = p.red_w;
-    a.red_argv = p.red_argv;
+    a.red_w = reinterpret_cast<T*>(p.red_w);
+    a.red_argv = reinterpret_cast<long long*>(p.red_argv);
     a.red_argi = p.red_argi;
     a.alpha_slot = p.alpha_slot;
     a.bar = p.bar;
     a.err = p.err;
     a.timeout_ns = p.timeout_ns;
     a.flag_tol = p.flag_tol;
-    a.xcap = panel_xcap<T>();
+    a.xcap = panel_xcap<T>(nb);
     const int ncols = a.nend - j0;
-    int G = std::max(1, std::min(gcap, (ncols + 7) / 8));
-    a.gb = std::max(1, std::min(G, (m - j0 + 255) / 256));
+    // enough CTAs for both the per-step row work (phase B) and the trailing columns
+    int G = std::max(1, std::min(gcap, std::max((ncols + 7) / 8, (m - j0 + 63) / 64)));
     a.expected = (unsigned)G + p.barrier_extra;
     // algorithmic bytes: per step one read of the trailing block rows J..m
     double bytes = 0.0, flops = 0.0;
@@ -588,10 +922,16 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       bytes += rows * cols * sizeof(T);
       flops += 8.0 * rows * cols;
     }
+    // dynamic shared memory sized to the x vector this panel stages (rounded to
+    // 16 KB): the rest of the SM's unified L1/shared storage stays L1, which
+    // holds the trailing sweep's loads in flight
+    const int need = (int)std::min<int64_t>((int64_t)(m - j0 + 2) * sizeof(T), smem);
+    const int dyn = std::min(smem, (need + 16383) / 16384 * 16384);
+    a.xcap = dyn / (int)sizeof(T);
     void* args[] = {&a};
-    hook_before(hooks, MPS_KCLASS_PANEL, bytes, flops);
-    CK(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<T>, dim3(G), dim3(PNT), args, (size_t)smem, s));
-    hook_after(hooks, MPS_KCLASS_PANEL, 1);
+    hook_before(hooks, K(MPS_KCLASS_PANEL), bytes, flops);
+    CK(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<T>, dim3(G), dim3(PNT), args, (size_t)dyn, s));
+    hook_after(hooks, K(MPS_KCLASS_PANEL), 1);
     if (p.pivot) {
       if (J1 < n && J1 < m) {
         GemmDesc<T> d;
@@ -613,20 +953,24 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
         d.C = p.W + J1 + (int64_t)J1 * p.ldw;
         d.ldc = p.ldw;
         double M = d.M, N = d.N;
-        hook_before(hooks, MPS_KCLASS_UPDATE, (2.0 * M * N + (M + N) * kb) * sizeof(T), 8.0 * M * N * kb);
+        hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * N + (M + N) * kb) * sizeof(T), 8.0 * M * N * kb);
         CK(gemm_simt<T>(d, s));
-        hook_after(hooks, MPS_KCLASS_UPDATE, 1);
+        hook_after(hooks, K(MPS_KCLASS_UPDATE), 1);
       }
       if (J1 < n) {
-        hook_before(hooks, MPS_KCLASS_NORMS, (double)std::max(0, m - J1) * (n - J1) * sizeof(T),
+        hook_before(hooks, K(MPS_KCLASS_NORMS), (double)std::max(0, m - J1) * (n - J1) * sizeof(T),
                     3.0 * std::max(0, m - J1) * (n - J1));
         int warps = 8;
         col_norms_kernel<T><<<(n - J1 + warps - 1) / warps, warps * 32, 0, s>>>(p.W, p.ldw, m, J1, J1, n, p.vn1,
                                                                                p.vn2);
         CK(cudaGetLastError());
-        hook_after(hooks, MPS_KCLASS_NORMS, 1);
+        hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
       }
     } else if (J1 < n) {
+      hook_before(hooks, K(MPS_KCLASS_UPDATE), 0, 0);
+      tfactor_kernel<T><<<1, 128, 0, s>>>(p.Wg, p.tau, pi, k, nb, p.Tfac);
+      CK(cudaGetLastError());
+      hook_after(hooks, K(MPS_KCLASS_UPDATE), 1);
       // C = W[j0:m, J1:n] <- (I - V T V^H)^H C = C - V T^H (V^H C)
       const int M = m - j0, N = n - J1;
       GemmDesc<T> d;
@@ -646,9 +990,14 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       d.b_conj = 0;
       d.b_mask = MASK_NONE;
       d.C = p.Y;
-      d.ldc = nb;
-      hook_before(hooks, MPS_KCLASS_UPDATE, ((double)M * N + (double)M * kb) * sizeof(T), 8.0 * M * N * kb);
+      d.ldc = kb;
+      d.splitk = choose_splitk(kb, N, M, kMaxSplit);
+      d.wk = p.SK;
+      hook_before(hooks, K(MPS_KCLASS_UPDATE), ((double)M * N + (double)M * kb) * sizeof(T), 8.0 * M * N * kb);
+      int nl = gemm_launches(d);
       CK(gemm_simt<T>(d, s));
+      d.splitk = 0;
+      d.wk = nullptr;
       d.M = kb;
       d.N = N;
       d.K = kb;
@@ -658,9 +1007,9 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       d.a_conj = 1;
       d.a_mask = MASK_NONE;
       d.B = p.Y;
-      d.ldb = nb;
+      d.ldb = kb;
       d.C = p.Z;
-      d.ldc = nb;
+      d.ldc = kb;
       CK(gemm_simt<T>(d, s));
       d.M = M;
       d.N = N;
@@ -673,18 +1022,27 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       d.a_conj = 0;
       d.a_mask = MASK_UNIT_LOWER;
       d.B = p.Z;
-      d.ldb = nb;
+      d.ldb = kb;
       d.C = p.W + j0 + (int64_t)J1 * p.ldw;
       d.ldc = p.ldw;
       CK(gemm_simt<T>(d, s));
-      hook_after(hooks, MPS_KCLASS_UPDATE, 3);
+      hook_after(hooks, K(MPS_KCLASS_UPDATE), 2 + nl);
     }
   }
+  {
+    // triangular factors for Q formation (panels not yet done by the unpivoted path)
+    const int first = p.pivot ? 0 : npanels - 1;
+    const int cnt = p.pivot ? npanels : 1;
+    hook_before(hooks, K(MPS_KCLASS_FORMQ), 0, 0);
+    tfactor_kernel<T><<<cnt, 128, 0, s>>>(p.Wg, p.tau, first, k, nb, p.Tfac);
+    CK(cudaGetLastError());
+    hook_after(hooks, K(MPS_KCLASS_FORMQ), 1);
+  }
   if (p.pivot && p.discarded) {
-    hook_before(hooks, MPS_KCLASS_NORMS, 8.0 * (n - k), 0);
+    hook_before(hooks, K(MPS_KCLASS_NORMS), 8.0 * (n - k), 0);
     discarded_kernel<<<1, 256, 0, s>>>(p.vn1, k, n, p.discarded, p.disc_total);
     CK(cudaGetLastError());
-    hook_after(hooks, MPS_KCLASS_NORMS, 1);
+    hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
   }
   return cudaSuccess;
 }
@@ -692,11 +1050,12 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
 template <typename T>
 cudaError_t qr_form_q(const QrPlan<T>& p, T* Q, int64_t ldq, cudaStream_t s, LaunchHooks* hooks) {
   using R = typename real_of<T>::type;
+  const ClassMap K{p.kclass};
   const int m = p.m, k = p.k, nb = p.nb;
   if (k <= 0) return cudaSuccess;
-  hook_before(hooks, MPS_KCLASS_FORMQ, (double)m * k * sizeof(T), 0);
+  hook_before(hooks, K(MPS_KCLASS_FORMQ), (double)m * k * sizeof(T), 0);
   CK(set_identity<T>(Q, ldq, m, k, s));
-  hook_after(hooks, MPS_KCLASS_FORMQ, 1);
+  hook_after(hooks, K(MPS_KCLASS_FORMQ), 1);
   const int npanels = (k + nb - 1) / nb;
   for (int pi = npanels - 1; pi >= 0; --pi) {
     const int j0 = pi * nb;
@@ -721,9 +1080,14 @@ cudaError_t qr_form_q(const QrPlan<T>& p, T* Q, int64_t ldq, cudaStream_t s, Lau
     d.b_conj = 0;
     d.b_mask = MASK_NONE;
     d.C = p.Y;
-    d.ldc = nb;
-    hook_before(hooks, MPS_KCLASS_FORMQ, (2.0 * M * N + 2.0 * M * kb) * sizeof(T), 16.0 * M * N * kb);
+    d.ldc = kb;
+    d.splitk = choose_splitk(kb, N, M, kMaxSplit);
+    d.wk = p.SK;
+    hook_before(hooks, K(MPS_KCLASS_FORMQ), (2.0 * M * N + 2.0 * M * kb) * sizeof(T), 16.0 * M * N * kb);
+    int nl = gemm_launches(d);
     CK(gemm_simt<T>(d, s));
+    d.splitk = 0;
+    d.wk = nullptr;
     // Z = T Y
     d.M = kb;
     d.N = N;
@@ -734,9 +1098,9 @@ cudaError_t qr_form_q(const QrPlan<T>& p, T* Q, int64_t ldq, cudaStream_t s, Lau
     d.a_conj = 0;
     d.a_mask = MASK_NONE;
     d.B = p.Y;
-    d.ldb = nb;
+    d.ldb = kb;
     d.C = p.Z;
-    d.ldc = nb;
+    d.ldc = kb;
     CK(gemm_simt<T>(d, s));
     // Q[j0:m, j0:k] -= V Z
     d.M = M;
@@ -750,11 +1114,11 @@ cudaError_t qr_form_q(const QrPlan<T>& p, T* Q, int64_t ldq, cudaStream_t s, Lau
     d.a_conj = 0;
     d.a_mask = MASK_UNIT_LOWER;
     d.B = p.Z;
-    d.ldb = nb;
+    d.ldb = kb;
     d.C = Q + j0 + (int64_t)j0 * ldq;
     d.ldc = ldq;
     CK(gemm_simt<T>(d, s));
-    hook_after(hooks, MPS_KCLASS_FORMQ, 3);
+    hook_after(hooks, K(MPS_KCLASS_FORMQ), 2 + nl);
   }
   return cudaSuccess;
 }

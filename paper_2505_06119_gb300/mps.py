@@ -133,11 +133,14 @@ class MPS:
         self._check(self.lib.mps_bond_dims(self.h, arr))
         return list(arr)
 
-    def get_site(self, i, fmt="c128"):
+    def get_site(self, i, fmt="c128", out=None):
         b = self.bond_dims()
         shape = (b[i], 2, b[i + 1])
         dt = np.complex128 if fmt == "c128" else np.complex64
-        out = np.empty(shape, dtype=dt)
+        if out is None:
+            out = np.empty(shape, dtype=dt)
+        elif out.shape != shape or out.dtype != dt or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous %s array of shape %s" % (dt, shape))
         code = L.MPS_HOST_C128 if fmt == "c128" else L.MPS_HOST_C64
         self._check(self.lib.mps_get_site(self.h, i, code, out.ctypes.data, out.size))
         return out
