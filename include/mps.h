@@ -77,7 +77,12 @@ extern "C" {
 #define MPS_HOST_C64 1
 
 /* mps_config.flags */
-#define MPS_FLAG_PROFILE 1 /* time the tracked kernels with CUDA events (mps_kernel_stats) */
+#define MPS_FLAG_PROFILE 1          /* time the tracked kernels with CUDA events (mps_kernel_stats) */
+#define MPS_FLAG_TENSOR_CORES 2     /* mixed precision: long-K complex products (theta, centre-move
+                                       absorption) on the tcgen05 tensor cores with 3xTF32 splitting.
+                                       Off by default: the tensor cores' FP32 accumulation drifts
+                                       linearly with K (about 6e-5 relative at K = 4096 on GB300),
+                                       above the CUDA-core path's 1e-7. */
 
 typedef struct mps_s* mps_t;
 typedef struct {
@@ -230,6 +235,18 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
                        const void* A, const void* B, const mps_c128 g[16], void* A_out,
                        void* B_out, double* discarded_dev, void* workspace, size_t ws_bytes,
                        void* stream);
+
+/* Built-in self-test of the tensor-core complex64 GEMM against the CUDA-core
+ * one on seeded random operands (diagnostic; allocates its own device memory
+ * on the current device and synchronises it).  theta = 0: C = alpha*op(A)op(B)
+ * + beta*C, M x N x K, with the operand views of the library's GEMM: a_row
+ * (A(i,k) = A[i*K + k], else A[i + k*M]), b_row (B(k,j) = B[k*N + j], else
+ * B[k + j*K]), conj flags and masks (0 none, 1 unit lower, 2 upper).
+ * theta = 1: the theta contraction with a fixed gate, chi_l = M, chi_r = N,
+ * chi_m = K.  Outputs the largest absolute difference and the largest
+ * absolute reference entry. */
+int mps_selftest_gemm(int M, int N, int K, int a_row, int a_conj, int a_mask, int b_row, int b_conj, int b_mask,
+                      int theta, unsigned seed, double* max_abs_err, double* max_abs_ref);
 
 /* Library version (major*10000 + minor*100 + patch). */
 int mps_version(void);

@@ -25,6 +25,7 @@ MPS_POLICY_LOCAL = 1
 MPS_HOST_C128 = 0
 MPS_HOST_C64 = 1
 MPS_FLAG_PROFILE = 1
+MPS_FLAG_TENSOR_CORES = 2
 
 KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other", "canon"]
 
@@ -60,6 +61,8 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 SIGNATURES = {
     "mps_version": (_I, []),
+    "mps_selftest_gemm": (_I, [_I, _I, _I, _I, _I, _I, _I, _I, _I, _I, ctypes.c_uint,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mps_config_init": (None, [ctypes.POINTER(mps_config)]),
     "mps_create": (_I, [ctypes.POINTER(_P), _I, _I]),
     "mps_create_ex": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(mps_config)]),

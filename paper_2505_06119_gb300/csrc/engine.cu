@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -142,6 +143,7 @@ struct Knobs {
   double flag_tol;
   unsigned long long timeout_ns;
   unsigned barrier_extra;
+  bool use_tc;  // complex64 products on the tensor cores
 };
 
 template <typename T>
@@ -178,6 +180,7 @@ QrPlan<T> make_plan(const Ws<T>& w, const Knobs& kn, int m, int n, int k, int pi
   p.flag_tol = kn.flag_tol;
   p.timeout_ns = kn.timeout_ns;
   p.barrier_extra = kn.barrier_extra;
+  p.use_tc = kn.use_tc;
   return p;
 }
 
@@ -203,7 +206,14 @@ cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int c
   const int k = std::min(std::min(m, n), chi);
   hook_before(hk, MPS_KCLASS_THETA, ((double)m * cm + (double)cm * n + (double)m * n) * sizeof(T),
               8.0 * m * n * cm + 32.0 * m * n);
-  CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s));
+  if constexpr (std::is_same<T, c64>::value) {
+    if (kn.use_tc)
+      CKE(tc_theta(cl, cm, cr, A, B, g, w.W, w.ldw, w.err, kn.timeout_ns, s));
+    else
+      CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s));
+  } else {
+    CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s));
+  }
   hook_after(hk, MPS_KCLASS_THETA, 1);
   QrPlan<T> p = make_plan<T>(w, kn, m, n, k, 1, disc_slot, disc_total);
   CKE(qr_factor<T>(p, s, hk));
@@ -437,7 +447,7 @@ int move_right(mps_t h, int j) {
   d.ldc = 2 * cn;
   hook_before(hk, MPS_KCLASS_CANON, ((double)2 * cn * cr + (double)k * cr + 2.0 * cn * k) * sizeof(T),
               8.0 * 2 * cn * k * cr);
-  CUTRY(h, gemm_simt<T>(d, s), "move_right absorb");
+  CUTRY(h, gemm_auto<T>(d, h->kn.use_tc, w.err, h->kn.timeout_ns, s), "move_right absorb");
   hook_after(hk, MPS_KCLASS_CANON, 1);
   CUTRY(h, cudaMemcpyAsync(sn, w.Q, sizeof(T) * (size_t)k * 2 * cn, cudaMemcpyDeviceToDevice, s), "move_right copy");
   h->bond[j + 1] = k;
@@ -487,7 +497,7 @@ int move_left(mps_t h, int j) {
   d.ldc = k;
   hook_before(hk, MPS_KCLASS_CANON, ((double)2 * cp * cl + (double)k * cl + 2.0 * cp * k) * sizeof(T),
               8.0 * 2 * cp * k * cl);
-  CUTRY(h, gemm_simt<T>(d, s), "move_left absorb");
+  CUTRY(h, gemm_auto<T>(d, h->kn.use_tc, w.err, h->kn.timeout_ns, s), "move_left absorb");
   hook_after(hk, MPS_KCLASS_CANON, 1);
   CUTRY(h, cudaMemcpyAsync(sp, w.Q, sizeof(T) * (size_t)k * 2 * cp, cudaMemcpyDeviceToDevice, s), "move_left copy");
   h->bond[j] = k;
@@ -689,6 +699,101 @@ extern "C" {
 
 int mps_version(void) { return 100; }
 
+}  // extern "C"
+
+namespace {
+__global__ void fill_random_kernel(c64* p, int64_t n, unsigned seed) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t x = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  p[i] = mk<float>((float)((x & 0xffffff) / 8388608.0 - 1.0), (float)(((x >> 24) & 0xffffff) / 8388608.0 - 1.0));
+}
+}  // namespace
+
+extern "C" {
+
+int mps_selftest_gemm(int M, int N, int K, int a_row, int a_conj, int a_mask, int b_row, int b_conj, int b_mask,
+                      int theta, unsigned seed, double* max_abs_err, double* max_abs_ref) {
+  if (M < 1 || N < 1 || K < 1 || !max_abs_err || !max_abs_ref) return MPS_E_ARG;
+  const int64_t na = (int64_t)(theta ? 2 * M : M) * K, nb = (int64_t)K * (theta ? 2 * N : N);
+  const int64_t nc = theta ? (int64_t)(2 * M) * (2 * N) : (int64_t)M * N;
+  c64 *A = nullptr, *B = nullptr, *C1 = nullptr, *C2 = nullptr;
+  int* err = nullptr;
+  int rc = MPS_OK;
+  if (cudaMalloc(&A, sizeof(c64) * na) != cudaSuccess || cudaMalloc(&B, sizeof(c64) * nb) != cudaSuccess ||
+      cudaMalloc(&C1, sizeof(c64) * nc) != cudaSuccess || cudaMalloc(&C2, sizeof(c64) * nc) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    rc = MPS_E_NOMEM;
+  } else {
+    cudaMemset(err, 0, sizeof(int));
+    fill_random_kernel<<<(unsigned)((na + 255) / 256), 256>>>(A, na, seed);
+    fill_random_kernel<<<(unsigned)((nb + 255) / 256), 256>>>(B, nb, seed + 17);
+    fill_random_kernel<<<(unsigned)((nc + 255) / 256), 256>>>(C1, nc, seed + 29);
+    cudaMemcpy(C2, C1, sizeof(c64) * nc, cudaMemcpyDeviceToDevice);
+    cudaError_t e1, e2;
+    if (theta) {
+      c64 g[16];
+      for (int i = 0; i < 16; ++i) g[i] = mk<float>(0.25f * ((i * 7) % 5 - 2), 0.125f * ((i * 3) % 7 - 3));
+      e1 = tc_theta(M, K, N, A, B, g, C1, 2 * M, err, 10000000000ull, 0);
+      e2 = theta_gemm_simt<c64>(M, K, N, A, B, g, C2, 2 * M, 0);
+    } else {
+      GemmDesc<c64> d;
+      d.M = M;
+      d.N = N;
+      d.K = K;
+      d.alpha = mk<float>(0.7f, 0.2f);
+      d.beta = mk<float>(0.3f, -0.5f);
+      d.A = A;
+      d.lda = a_row ? K : M;
+      d.a_row = a_row;
+      d.a_conj = a_conj;
+      d.a_mask = a_mask;
+      d.B = B;
+      d.ldb = b_row ? N : K;
+      d.b_row = b_row;
+      d.b_conj = b_conj;
+      d.b_mask = b_mask;
+      d.C = C1;
+      d.ldc = M;
+      e1 = tc_gemm(d, err, 10000000000ull, 0);
+      d.C = C2;
+      e2 = gemm_simt<c64>(d, 0);
+    }
+    cudaError_t e3 = cudaDeviceSynchronize();
+    int herr = 0;
+    cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      rc = MPS_E_CUDA;
+    } else if (herr != 0) {
+      rc = MPS_E_TIMEOUT;
+    } else {
+      std::vector<c64> h1(nc), h2(nc);
+      cudaMemcpy(h1.data(), C1, sizeof(c64) * nc, cudaMemcpyDeviceToHost);
+      cudaMemcpy(h2.data(), C2, sizeof(c64) * nc, cudaMemcpyDeviceToHost);
+      double me = 0, mr = 0;
+      for (int64_t i = 0; i < nc; ++i) {
+        me = std::max(me, (double)std::fabs(h1[i].re - h2[i].re));
+        me = std::max(me, (double)std::fabs(h1[i].im - h2[i].im));
+        mr = std::max(mr, (double)std::fabs(h2[i].re));
+        mr = std::max(mr, (double)std::fabs(h2[i].im));
+      }
+      *max_abs_err = me;
+      *max_abs_ref = mr;
+    }
+  }
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(C1);
+  cudaFree(C2);
+  cudaFree(err);
+  return rc;
+}
+
 void mps_config_init(mps_config* cfg) {
   if (!cfg) return;
   memset(cfg, 0, sizeof(*cfg));
@@ -732,6 +837,7 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   }
   h->kn.barrier_extra = (unsigned)cfg.debug_barrier_extra;
   h->prof.enabled = (cfg.flags & MPS_FLAG_PROFILE) != 0;
+  h->kn.use_tc = h->prec == MPS_PREC_MIXED && (cfg.flags & MPS_FLAG_TENSOR_CORES) != 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -1124,6 +1230,7 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
   kn.flag_tol = precision == MPS_PREC_FP64 ? 1.4901161193847656e-08 : 1e-3;
   kn.timeout_ns = 10000000000ull;
   kn.barrier_extra = 0;
+  kn.use_tc = false;
   double* slot = discarded_dev ? discarded_dev : (double*)(base + L.disc);
   cudaError_t e;
   if (precision == MPS_PREC_FP64) {

@@ -3,6 +3,7 @@
 // moves and contractions, and the theta contraction with its fused gate
 // epilogue (Sec. III-B.1 bond contraction, Sec. III-C.2 tensor application).
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -345,6 +346,16 @@ cudaError_t theta_gemm_simt(int chi_l, int chi_m, int chi_r, const T* A, const T
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t gemm_auto(const GemmDesc<T>& d, bool use_tc, int* err, unsigned long long timeout_ns, cudaStream_t s) {
+  if constexpr (std::is_same<T, c64>::value) {
+    if (use_tc && tc_gemm_applicable(d)) return tc_gemm(d, err, timeout_ns, s);
+  }
+  return gemm_simt<T>(d, s);
+}
+
+template cudaError_t gemm_auto<c64>(const GemmDesc<c64>&, bool, int*, unsigned long long, cudaStream_t);
+template cudaError_t gemm_auto<c128>(const GemmDesc<c128>&, bool, int*, unsigned long long, cudaStream_t);
 template cudaError_t gemm_simt<c64>(const GemmDesc<c64>&, cudaStream_t);
 template cudaError_t gemm_simt<c128>(const GemmDesc<c128>&, cudaStream_t);
 template cudaError_t theta_gemm_simt<c64>(int, int, int, const c64*, const c64*, const c64*, c64*,

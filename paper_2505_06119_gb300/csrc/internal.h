@@ -50,6 +50,18 @@ int gemm_launches(const GemmDesc<T>& d) {
 // split count that fills the GPU for a skinny product (few output tiles, long K)
 int choose_splitk(int M, int N, int K, int max_split);
 
+// Tensor-core (tcgen05, 3xTF32) complex64 GEMM with the same operand views
+// as gemm_simt (no split-K); a wait that expires sets *err.
+bool tc_gemm_applicable(const GemmDesc<c64>& d);
+cudaError_t tc_gemm(const GemmDesc<c64>& d, int* err, unsigned long long timeout_ns, cudaStream_t s);
+cudaError_t tc_theta(int cl, int cm, int cr, const c64* A, const c64* B, const c64* g16, c64* W, int64_t ldw,
+                     int* err, unsigned long long timeout_ns, cudaStream_t s);
+
+// GEMM dispatch: complex64 products go to the tensor cores when `use_tc` and
+// the shape suits them, everything else to gemm_simt.
+template <typename T>
+cudaError_t gemm_auto(const GemmDesc<T>& d, bool use_tc, int* err, unsigned long long timeout_ns, cudaStream_t s);
+
 // theta contraction with the gate epilogue (Sec. III-B.1 + III-C.2):
 //   X[(l,c),(d,r)] = sum_mu A[l,c,mu] B[mu,d,r]
 //   W[(b*chi_r + r)*ldw + 2l + a] = sum_{cd} g[2a+b][2c+d] X[(l,c),(d,r)]
@@ -125,6 +137,7 @@ struct QrPlan {
   unsigned long long timeout_ns;
   unsigned barrier_extra;  // 0 normally; >0 only to exercise the timeout path
   int kclass = -1;         // >= 0: attribute every launch to this kernel class
+  bool use_tc = false;     // complex64 GEMMs on the tensor cores
 };
 
 struct LaunchHooks;  // profiling hooks (engine.cu)

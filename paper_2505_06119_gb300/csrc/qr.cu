@@ -263,7 +263,11 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   T* W = a.W;
   const int64_t ldw = a.ldw;
   // an earlier bounded wait expired: the factorisation is void, leave at once
-  if (ld_relaxed_i32(a.err) != DEV_OK) return;
+  // (decided once for the whole CTA)
+  __shared__ int s_skip;
+  if (tid == 0) s_skip = ld_relaxed_i32(a.err) != DEV_OK;
+  __syncthreads();
+  if (s_skip) return;
 
   // Phase 0: partial argmax over this CTA's share of [j0, nend)
   if (a.pivot) {
@@ -954,7 +958,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
         d.ldc = p.ldw;
         double M = d.M, N = d.N;
         hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * N + (M + N) * kb) * sizeof(T), 8.0 * M * N * kb);
-        CK(gemm_simt<T>(d, s));
+        CK(gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s));
         hook_after(hooks, K(MPS_KCLASS_UPDATE), 1);
       }
       if (J1 < n) {
@@ -1025,7 +1029,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       d.ldb = kb;
       d.C = p.W + j0 + (int64_t)J1 * p.ldw;
       d.ldc = p.ldw;
-      CK(gemm_simt<T>(d, s));
+      CK(gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s));
       hook_after(hooks, K(MPS_KCLASS_UPDATE), 2 + nl);
     }
   }
@@ -1117,7 +1121,7 @@ cudaError_t qr_form_q(const QrPlan<T>& p, T* Q, int64_t ldq, cudaStream_t s, Lau
     d.ldb = kb;
     d.C = Q + j0 + (int64_t)j0 * ldq;
     d.ldc = ldq;
-    CK(gemm_simt<T>(d, s));
+    CK(gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s));
     hook_after(hooks, K(MPS_KCLASS_FORMQ), 2 + nl);
   }
   return cudaSuccess;

@@ -29,7 +29,7 @@ def _gate(g, n):
 
 
 def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile=False,
-           wait_timeout_s=0.0, device=0, debug_barrier_extra=0):
+           wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False):
     lib = L.load()
     cfg = L.mps_config()
     lib.mps_config_init(ctypes.byref(cfg))
@@ -37,7 +37,7 @@ def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile
     cfg.policy = {"canon": L.MPS_POLICY_CANON, "local": L.MPS_POLICY_LOCAL}[policy]
     cfg.panel_width = panel_width
     cfg.stream = stream
-    cfg.flags = L.MPS_FLAG_PROFILE if profile else 0
+    cfg.flags = (L.MPS_FLAG_PROFILE if profile else 0) | (L.MPS_FLAG_TENSOR_CORES if tensor_cores else 0)
     cfg.wait_timeout_s = wait_timeout_s
     cfg.device = device
     cfg.debug_barrier_extra = debug_barrier_extra
