@@ -236,6 +236,33 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
                        void* B_out, double* discarded_dev, void* workspace, size_t ws_bytes,
                        void* stream);
 
+/* Workspace size of mps_two_site_apply_noalloc: 16 MiB. */
+#define MPS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* mps_two_site_apply for callers that must not allocate device memory at all:
+ * code that runs inside someone else's memory manager (an allocator callback,
+ * a framework that owns every byte of the GPU), or a loop with a fixed memory
+ * budget where a cudaMalloc could fail or synchronise the device at the wrong
+ * moment.  The paper has no counterpart; this is a convenience of the library.
+ *
+ * Arguments and results are those of mps_two_site_apply minus the workspace:
+ * the scratch space is one fixed device array inside the library,
+ * MPS_NOALLOC_SCRATCH_BYTES long, which every GPU that loads the library keeps
+ * until the process exits.  The call returns MPS_E_UNSUPPORTED, doing nothing,
+ * when mps_two_site_workspace reports more than that (complex128 bonds of a
+ * few hundred, complex64 ones somewhat larger).  The caller still owns and
+ * passes A, B, A_out, B_out and discarded_dev.
+ * All calls share that one array and it keeps whatever the last call left in
+ * it (every call clears the parts that must start at zero itself): two calls
+ * whose GPU work overlaps, on different streams or from threads the caller
+ * does not order, race on it and must be serialised by the caller.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture begins. */
+int mps_two_site_apply_noalloc(int precision, int chi_l, int chi_m, int chi_r, int chi_max, const void* A,
+                               const void* B, const mps_c128 g[16], void* A_out, void* B_out,
+                               double* discarded_dev, void* stream);
+
 /* Built-in self-test of the tensor-core complex64 GEMM against the CUDA-core
  * one on seeded random operands (diagnostic; allocates its own device memory
  * on the current device and synchronises it).  theta = 0: C = alpha*op(A)op(B)

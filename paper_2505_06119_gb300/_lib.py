@@ -26,6 +26,7 @@ MPS_HOST_C128 = 0
 MPS_HOST_C64 = 1
 MPS_FLAG_PROFILE = 1
 MPS_FLAG_TENSOR_CORES = 2
+MPS_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other", "canon"]
 
@@ -90,6 +91,8 @@ SIGNATURES = {
     "mps_two_site_workspace": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "mps_two_site_apply": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.POINTER(mps_c128), _P, _P,
                                 _P, _P, ctypes.c_size_t, _P]),
+    "mps_two_site_apply_noalloc": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.POINTER(mps_c128), _P, _P,
+                                        _P, _P]),
 }
 
 _lib = None

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -693,6 +694,17 @@ bool valid_site(mps_t h, int i) { return i >= 0 && i < h->n; }
 
 }  // namespace
 
+// Scratch space of mps_two_site_apply_noalloc.  In host code this name is only
+// a stand-in for the device array: its device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MPS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocDevices] = {};
+}  // namespace
+
 // ===========================================================================
 // C ABI
 extern "C" {
@@ -1246,6 +1258,32 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
   }
   (void)k;
   return e == cudaSuccess ? MPS_OK : MPS_E_CUDA;
+}
+
+int mps_two_site_apply_noalloc(int precision, int chi_l, int chi_m, int chi_r, int chi_max, const void* A,
+                               const void* B, const mps_c128 g[16], void* A_out, void* B_out,
+                               double* discarded_dev, void* stream) {
+  size_t need = 0;
+  int rc = mps_two_site_workspace(precision, chi_l, chi_m, chi_r, chi_max, &need);
+  if (rc) return rc;
+  if (need > (size_t)MPS_NOALLOC_SCRATCH_BYTES) return MPS_E_UNSUPPORTED;  // beyond the fixed array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocDevices) return MPS_E_CUDA;
+  void* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return MPS_E_CUDA;
+      }
+      g_noalloc_ptr[dev] = p;
+    }
+    ws = g_noalloc_ptr[dev];
+  }
+  return mps_two_site_apply(precision, chi_l, chi_m, chi_r, chi_max, A, B, g, A_out, B_out, discarded_dev, ws,
+                            (size_t)MPS_NOALLOC_SCRATCH_BYTES, stream);
 }
 
 }  // extern "C"
