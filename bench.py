@@ -140,6 +140,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# DRAM traffic of the panel kernel from one ncu capture (profiles/qr_panel_kernel_chi2048.md):
+# dram bytes / algorithmic bytes of the captured launch.  Traffic scales with the
+# algorithmic bytes (both are sums over the trailing block), so a launch's traffic is
+# this ratio times its algorithmic bytes.  Valid only for the kernel source it was
+# measured on (sha256 of csrc/qr.cu); otherwise reported as null.
+PANEL_NCU = {"qr_cu_sha256": "c9a14c4d8d20937ef8918ce6d3656f7f6391a921b378621f0dec9e394ecf212f",
+             "dram_over_algorithmic": 0.9786}
+
+
+def panel_traffic(alg_bytes_per_launch):
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "paper_2505_06119_gb300", "csrc", "qr.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if sha != PANEL_NCU["qr_cu_sha256"]:
+        return None
+    return PANEL_NCU["dram_over_algorithmic"] * alg_bytes_per_launch
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -265,7 +287,9 @@ def ours(args):
                          "steps": args.fp64_warmup + args.fp64_steps, "f_fp64": f64, "f_mixed": fmx},
         "roofline": {"bound": "hbm", "kernel": "qr_panel_kernel (pivoted-QR panel: per-step trailing GEMV)",
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                     "frac": achieved / peaks.get("hbm_gbs", 1.0), "traffic": None,
+                     "frac": achieved / peaks.get("hbm_gbs", 1.0),
+                     "traffic": panel_traffic(panel["alg_bytes"] / max(1, panel["launches"])),
+                     "traffic_unit": "bytes per launch",
                      "peak_source": peak_src,
                      "launches_timed": panel["launches"], "kernel_ms_per_step": panel["ms"] / args.steps},
         "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in st.items()},
