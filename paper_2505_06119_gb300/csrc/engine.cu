@@ -41,7 +41,7 @@ int max_bond(int n, int b, int chi) {
 // ---------------------------------------------------------------------------
 // workspace of one two-site split (either precision); carved from one buffer
 struct WsLayout {
-  size_t W, Q, F, vn1, vn2, jpvt, inv, tau, Tfac, Wg, Y, Z, SK, red_norm, red_w, red_argv, red_argi, alpha,
+  size_t W, Q, F, vn1, vn2, jpvt, inv, tau, Tfac, Wg, Tblk, G12, Y, Z, SK, red_norm, red_w, red_argv, red_argi, alpha,
       bar, err, disc, total;
 };
 
@@ -67,9 +67,11 @@ WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int6
   L.tau = take(esz * (size_t)std::max(kmax, 1));
   L.Tfac = take(esz * (size_t)std::max(npan, 1) * nb * nb);
   L.Wg = take(16 * (size_t)std::max(npan, 1) * nb * nb);
-  L.Y = take(esz * (size_t)nb * std::max(wide, 1));
-  L.Z = take(esz * (size_t)nb * std::max(wide, 1));
-  L.SK = take(esz * (size_t)kMaxSplit * nb * std::max(wide, 1));
+  L.Tblk = take(esz * (size_t)(npan / 2 + 1) * 4 * nb * nb);
+  L.G12 = take(esz * (size_t)nb * nb);
+  L.Y = take(esz * (size_t)2 * nb * std::max(wide, 1));
+  L.Z = take(esz * (size_t)2 * nb * std::max(wide, 1));
+  L.SK = take(esz * (size_t)kMaxSplit * 2 * nb * std::max(wide, 1));
   L.red_norm = take(8 * (size_t)G);
   L.red_w = take(16 * (size_t)G * nb);
   L.red_argv = take(8 * (size_t)G);
@@ -96,6 +98,8 @@ struct Ws {
   T* tau;
   T* Tfac;
   c128* Wg;
+  T* Tblk;
+  T* G12;
   T* Y;
   T* Z;
   T* SK;
@@ -124,6 +128,8 @@ Ws<T> ws_views(char* base, const WsLayout& L, int64_t ldw, int64_t ldq) {
   w.tau = (T*)(base + L.tau);
   w.Tfac = (T*)(base + L.Tfac);
   w.Wg = (c128*)(base + L.Wg);
+  w.Tblk = (T*)(base + L.Tblk);
+  w.G12 = (T*)(base + L.G12);
   w.Y = (T*)(base + L.Y);
   w.Z = (T*)(base + L.Z);
   w.SK = (T*)(base + L.SK);
@@ -162,6 +168,8 @@ QrPlan<T> make_plan(const Ws<T>& w, const Knobs& kn, int m, int n, int k, int pi
   p.jpvt = w.jpvt;
   p.Tfac = w.Tfac;
   p.Wg = w.Wg;
+  p.Tblk = w.Tblk;
+  p.G12 = w.G12;
   p.F = w.F;
   p.vn1 = w.vn1;
   p.vn2 = w.vn2;

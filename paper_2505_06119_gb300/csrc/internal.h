@@ -129,9 +129,11 @@ struct QrPlan {
   int* err;           // device error word
   double* discarded;  // out: ||W[k:m, k:n]||_F^2 (pivot mode)
   double* disc_total; // optional: discarded is also added here
-  T* Y;               // nb * max(n, k) scratch for block-reflector GEMMs
-  T* Z;               // nb * max(n, k)
-  T* SK;              // split-K partials: kMaxSplit * nb * max(n, k)
+  T* Tblk;            // ceil(npanels/2) * (2nb)^2: factors of outer blocks of two panels
+  T* G12;             // nb * nb Gram block V1^H V2
+  T* Y;               // 2nb * max(n, k) scratch for block-reflector GEMMs
+  T* Z;               // 2nb * max(n, k)
+  T* SK;              // split-K partials: kMaxSplit * 2nb * max(n, k)
   int G;              // cooperative grid size cap
   double flag_tol;    // norm-downdate recompute threshold
   unsigned long long timeout_ns;

@@ -760,6 +760,36 @@ __device__ __forceinline__ double warp_norm2<c128>(const c128* __restrict__ col,
   return warp_sum(a + b);
 }
 
+// Triangular factor of two consecutive panels as one block reflector:
+// (I - V1 T1 V1^H)(I - V2 T2 V2^H) = I - V T V^H with V = [V1 V2] and
+// T = [[T1, -T1 (V1^H V2) T2], [0, T2]].  T1 (k1 x k1), T2 (k2 x k2) and
+// G12 = V1^H V2 (k1 x k2) are column-major with leading dims ld1, ld2, ldg;
+// T is written column-major with leading dim ldT.  One CTA of 1024 threads.
+template <typename T>
+__global__ void tmerge_kernel(const T* T1, int ld1, int k1, const T* T2, int ld2, int k2, const T* G12, int ldg,
+                              T* Tout, int ldT) {
+  using R = typename real_of<T>::type;
+  __shared__ T s_t1[32][33], s_t2[32][33], s_g[32][33], s_x[32][33];
+  const int i = threadIdx.x % 32, j = threadIdx.x / 32;
+  const T z = mk<R>(0, 0);
+  s_t1[i][j] = (i < k1 && j < k1) ? T1[i + (int64_t)j * ld1] : z;
+  s_t2[i][j] = (i < k2 && j < k2) ? T2[i + (int64_t)j * ld2] : z;
+  s_g[i][j] = (i < k1 && j < k2) ? G12[i + (int64_t)j * ldg] : z;
+  __syncthreads();
+  T acc = z;  // (T1 G12)[i][j]
+  for (int l = 0; l < 32; ++l) cfma(acc, s_t1[i][l], s_g[l][j]);
+  s_x[i][j] = acc;
+  __syncthreads();
+  acc = z;  // (T1 G12 T2)[i][j]
+  for (int l = 0; l < 32; ++l) cfma(acc, s_x[i][l], s_t2[l][j]);
+  const int kt = k1 + k2;
+  if (i < k1 && j < k1) Tout[i + (int64_t)j * ldT] = s_t1[i][j];
+  if (i < k2 && j < k2) Tout[k1 + i + (int64_t)(k1 + j) * ldT] = s_t2[i][j];
+  if (i < k1 && j < k2) Tout[i + (int64_t)(k1 + j) * ldT] = z - acc;
+  if (i < k2 && j < k1) Tout[k1 + i + (int64_t)j * ldT] = z;
+  (void)kt;
+}
+
 // vn1[t] = vn2[t] = ||W[r0:m, t]||^2 for t in [c0, n): one warp per column.
 template <typename T>
 __global__ void col_norms_kernel(const T* W, int64_t ldw, int m, int r0, int c0, int n, double* vn1,
@@ -847,6 +877,117 @@ struct ClassMap {
   int operator()(int c) const { return over >= 0 ? over : c; }
 };
 
+// Block reflector of the outer block starting at panel `pi` (panels pi and
+// pi+1 when both exist): T (kbb x kbb, leading dim 2 nb) into p.Tblk[pi / 2],
+// from the per-panel factors and the Gram block V1^H V2.  Returns the block
+// width kbb.  Launch count added to *nl.
+template <typename T>
+static cudaError_t outer_tfactor(const QrPlan<T>& p, int pi, int* kbb_out, int* nl, cudaStream_t s) {
+  using R = typename real_of<T>::type;
+  const int nb = p.nb, k = p.k, m = p.m, ob = 2 * nb;
+  const int j0 = pi * nb;
+  const int k1 = std::min(nb, k - j0);
+  const int k2 = std::max(0, std::min(nb, k - j0 - nb));
+  T* Tb = p.Tblk + (size_t)(pi / 2) * ob * ob;
+  const T* T1 = p.Tfac + (size_t)pi * nb * nb;
+  const T* T2 = p.Tfac + (size_t)(pi + 1) * nb * nb;
+  if (k2 > 0) {
+    // G12 = V1^H V2 over the rows where V2 is nonzero (rows >= j0 + nb)
+    GemmDesc<T> d;
+    d.M = k1;
+    d.N = k2;
+    d.K = m - (j0 + nb);
+    d.alpha = mk<R>(1, 0);
+    d.beta = mk<R>(0, 0);
+    d.A = p.W + (j0 + nb) + (int64_t)j0 * p.ldw;  // V1 rows >= j0+nb: plain (below V1's diagonal)
+    d.lda = p.ldw;
+    d.a_row = 1;
+    d.a_conj = 1;
+    d.a_mask = MASK_NONE;
+    d.B = p.W + (j0 + nb) + (int64_t)(j0 + nb) * p.ldw;  // V2, unit lower
+    d.ldb = p.ldw;
+    d.b_row = 0;
+    d.b_conj = 0;
+    d.b_mask = MASK_UNIT_LOWER;
+    d.C = p.G12;
+    d.ldc = nb;
+    d.splitk = choose_splitk(k1, k2, d.K, kMaxSplit);
+    d.wk = p.SK;
+    *nl += gemm_launches(d);
+    CK(gemm_simt<T>(d, s));
+  }
+  tmerge_kernel<T><<<1, 1024, 0, s>>>(T1, nb, k1, T2, nb, k2, p.G12, nb, Tb, ob);
+  CK(cudaGetLastError());
+  *nl += 1;
+  *kbb_out = k1 + k2;
+  return cudaSuccess;
+}
+
+// Apply (I - V Tb V^H)^H (trans = 1) or (I - V Tb V^H) (trans = 0) to
+// C = X[j0:m, c0:c0+N] (column-major, ldx), V = W[j0:m, j0:j0+kbb] unit lower:
+//   Y = V^H C,  Z = Tb^H Y (or Tb Y),  C -= V Z.
+template <typename T>
+static cudaError_t apply_block(const QrPlan<T>& p, int j0, int kbb, const T* Tb, int ldT, int trans, T* X,
+                               int64_t ldx, int c0, int N, int* nl, cudaStream_t s) {
+  using R = typename real_of<T>::type;
+  if (N <= 0 || kbb <= 0) return cudaSuccess;
+  const int M = p.m - j0;
+  GemmDesc<T> d;
+  d.M = kbb;
+  d.N = N;
+  d.K = M;
+  d.alpha = mk<R>(1, 0);
+  d.beta = mk<R>(0, 0);
+  d.A = p.W + j0 + (int64_t)j0 * p.ldw;  // V^H
+  d.lda = p.ldw;
+  d.a_row = 1;
+  d.a_conj = 1;
+  d.a_mask = MASK_UNIT_LOWER;
+  d.B = X + j0 + (int64_t)c0 * ldx;
+  d.ldb = ldx;
+  d.b_row = 0;
+  d.b_conj = 0;
+  d.b_mask = MASK_NONE;
+  d.C = p.Y;
+  d.ldc = kbb;
+  d.splitk = choose_splitk(kbb, N, M, kMaxSplit);
+  d.wk = p.SK;
+  *nl += gemm_launches(d);
+  CK(gemm_simt<T>(d, s));
+  d.splitk = 0;
+  d.wk = nullptr;
+  d.M = kbb;
+  d.N = N;
+  d.K = kbb;
+  d.A = Tb;
+  d.lda = ldT;
+  d.a_row = trans ? 1 : 0;
+  d.a_conj = trans ? 1 : 0;
+  d.a_mask = MASK_NONE;
+  d.B = p.Y;
+  d.ldb = kbb;
+  d.C = p.Z;
+  d.ldc = kbb;
+  *nl += 1;
+  CK(gemm_simt<T>(d, s));
+  d.M = M;
+  d.N = N;
+  d.K = kbb;
+  d.alpha = mk<R>(-1, 0);
+  d.beta = mk<R>(1, 0);
+  d.A = p.W + j0 + (int64_t)j0 * p.ldw;  // V
+  d.lda = p.ldw;
+  d.a_row = 0;
+  d.a_conj = 0;
+  d.a_mask = MASK_UNIT_LOWER;
+  d.B = p.Z;
+  d.ldb = kbb;
+  d.C = X + j0 + (int64_t)c0 * ldx;
+  d.ldc = ldx;
+  *nl += 1;
+  return gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s);
+}
+
 template <typename T>
 cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
   using R = typename real_of<T>::type;
@@ -884,6 +1025,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
   }
   const int smem = kPanelSmem;
+  int tblk_done = 0;  // outer blocks whose factor the unpivoted trailing updates already built
   for (int pi = 0; pi < npanels; ++pi) {
     const int j0 = pi * nb;
     const int kb = std::min(nb, k - j0);
@@ -971,76 +1113,45 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
         hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
       }
     } else if (J1 < n) {
-      hook_before(hooks, K(MPS_KCLASS_UPDATE), 0, 0);
+      // two-level blocking: panels are paired into outer blocks of 2 nb columns;
+      // the first panel of a pair updates only its partner's columns, the pair's
+      // combined block reflector then updates everything to the right.
+      int nl = 1;
+      const bool first_of_pair = (pi % 2 == 0) && (pi + 1 < npanels);
+      const int pb = pi - (pi % 2);  // first panel of this outer block
+      const int jb = first_of_pair ? j0 : pb * nb;
+      const int c0 = first_of_pair ? J1 : std::min(k, jb + 2 * nb);
+      const int c1 = first_of_pair ? std::min(k, j0 + 2 * nb) : n;  // partner columns only
+      const double M = m - jb, N = c1 - c0, kr = first_of_pair ? kb : c0 - jb;
+      hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * kr + 3.0 * M * N) * sizeof(T), 16.0 * M * N * kr);
       tfactor_kernel<T><<<1, 128, 0, s>>>(p.Wg, p.tau, pi, k, nb, p.Tfac);
       CK(cudaGetLastError());
-      hook_after(hooks, K(MPS_KCLASS_UPDATE), 1);
-      // C = W[j0:m, J1:n] <- (I - V T V^H)^H C = C - V T^H (V^H C)
-      const int M = m - j0, N = n - J1;
-      GemmDesc<T> d;
-      d.M = kb;
-      d.N = N;
-      d.K = M;
-      d.alpha = mk<R>(1, 0);
-      d.beta = mk<R>(0, 0);
-      d.A = p.W + j0 + (int64_t)j0 * p.ldw;  // V^H
-      d.lda = p.ldw;
-      d.a_row = 1;
-      d.a_conj = 1;
-      d.a_mask = MASK_UNIT_LOWER;
-      d.B = p.W + j0 + (int64_t)J1 * p.ldw;
-      d.ldb = p.ldw;
-      d.b_row = 0;
-      d.b_conj = 0;
-      d.b_mask = MASK_NONE;
-      d.C = p.Y;
-      d.ldc = kb;
-      d.splitk = choose_splitk(kb, N, M, kMaxSplit);
-      d.wk = p.SK;
-      hook_before(hooks, K(MPS_KCLASS_UPDATE), ((double)M * N + (double)M * kb) * sizeof(T), 8.0 * M * N * kb);
-      int nl = gemm_launches(d);
-      CK(gemm_simt<T>(d, s));
-      d.splitk = 0;
-      d.wk = nullptr;
-      d.M = kb;
-      d.N = N;
-      d.K = kb;
-      d.A = a.Tp;  // T^H
-      d.lda = nb;
-      d.a_row = 1;
-      d.a_conj = 1;
-      d.a_mask = MASK_NONE;
-      d.B = p.Y;
-      d.ldb = kb;
-      d.C = p.Z;
-      d.ldc = kb;
-      CK(gemm_simt<T>(d, s));
-      d.M = M;
-      d.N = N;
-      d.K = kb;
-      d.alpha = mk<R>(-1, 0);
-      d.beta = mk<R>(1, 0);
-      d.A = p.W + j0 + (int64_t)j0 * p.ldw;  // V
-      d.lda = p.ldw;
-      d.a_row = 0;
-      d.a_conj = 0;
-      d.a_mask = MASK_UNIT_LOWER;
-      d.B = p.Z;
-      d.ldb = kb;
-      d.C = p.W + j0 + (int64_t)J1 * p.ldw;
-      d.ldc = p.ldw;
-      CK(gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s));
-      hook_after(hooks, K(MPS_KCLASS_UPDATE), 2 + nl);
+      if (first_of_pair) {
+        CK(apply_block<T>(p, j0, kb, p.Tfac + (size_t)pi * nb * nb, nb, 1, p.W, p.ldw, c0, c1 - c0, &nl, s));
+      } else {
+        int kbb = 0;
+        CK(outer_tfactor<T>(p, pb, &kbb, &nl, s));
+        tblk_done = pb / 2 + 1;
+        CK(apply_block<T>(p, jb, kbb, p.Tblk + (size_t)(pb / 2) * 4 * nb * nb, 2 * nb, 1, p.W, p.ldw, c0, c1 - c0,
+                          &nl, s));
+      }
+      hook_after(hooks, K(MPS_KCLASS_UPDATE), nl);
     }
   }
   {
-    // triangular factors for Q formation (panels not yet done by the unpivoted path)
+    // triangular factors for Q formation: every panel's own factor (the
+    // unpivoted path already has all but the last), then the outer blocks
     const int first = p.pivot ? 0 : npanels - 1;
     const int cnt = p.pivot ? npanels : 1;
+    int nl = 1;
     hook_before(hooks, K(MPS_KCLASS_FORMQ), 0, 0);
     tfactor_kernel<T><<<cnt, 128, 0, s>>>(p.Wg, p.tau, first, k, nb, p.Tfac);
     CK(cudaGetLastError());
-    hook_after(hooks, K(MPS_KCLASS_FORMQ), 1);
+    for (int pb = 2 * tblk_done; pb < npanels; pb += 2) {
+      int kbb = 0;
+      CK(outer_tfactor<T>(p, pb, &kbb, &nl, s));
+    }
+    hook_after(hooks, K(MPS_KCLASS_FORMQ), nl);
   }
   if (p.pivot && p.discarded) {
     hook_before(hooks, K(MPS_KCLASS_NORMS), 8.0 * (n - k), 0);
@@ -1061,68 +1172,16 @@ cudaError_t qr_form_q(const QrPlan<T>& p, T* Q, int64_t ldq, cudaStream_t s, Lau
   CK(set_identity<T>(Q, ldq, m, k, s));
   hook_after(hooks, K(MPS_KCLASS_FORMQ), 1);
   const int npanels = (k + nb - 1) / nb;
-  for (int pi = npanels - 1; pi >= 0; --pi) {
-    const int j0 = pi * nb;
-    const int kb = std::min(nb, k - j0);
+  const int ob = 2 * nb;
+  const int nblk = (npanels + 1) / 2;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int j0 = bi * ob;
+    const int kbb = std::min(ob, k - j0);
     const int M = m - j0, N = k - j0;
-    const T* Tp = p.Tfac + (size_t)pi * nb * nb;
-    GemmDesc<T> d;
-    // Y = V^H Q[j0:m, j0:k]
-    d.M = kb;
-    d.N = N;
-    d.K = M;
-    d.alpha = mk<R>(1, 0);
-    d.beta = mk<R>(0, 0);
-    d.A = p.W + j0 + (int64_t)j0 * p.ldw;
-    d.lda = p.ldw;
-    d.a_row = 1;
-    d.a_conj = 1;
-    d.a_mask = MASK_UNIT_LOWER;
-    d.B = Q + j0 + (int64_t)j0 * ldq;
-    d.ldb = ldq;
-    d.b_row = 0;
-    d.b_conj = 0;
-    d.b_mask = MASK_NONE;
-    d.C = p.Y;
-    d.ldc = kb;
-    d.splitk = choose_splitk(kb, N, M, kMaxSplit);
-    d.wk = p.SK;
-    hook_before(hooks, K(MPS_KCLASS_FORMQ), (2.0 * M * N + 2.0 * M * kb) * sizeof(T), 16.0 * M * N * kb);
-    int nl = gemm_launches(d);
-    CK(gemm_simt<T>(d, s));
-    d.splitk = 0;
-    d.wk = nullptr;
-    // Z = T Y
-    d.M = kb;
-    d.N = N;
-    d.K = kb;
-    d.A = Tp;
-    d.lda = nb;
-    d.a_row = 0;
-    d.a_conj = 0;
-    d.a_mask = MASK_NONE;
-    d.B = p.Y;
-    d.ldb = kb;
-    d.C = p.Z;
-    d.ldc = kb;
-    CK(gemm_simt<T>(d, s));
-    // Q[j0:m, j0:k] -= V Z
-    d.M = M;
-    d.N = N;
-    d.K = kb;
-    d.alpha = mk<R>(-1, 0);
-    d.beta = mk<R>(1, 0);
-    d.A = p.W + j0 + (int64_t)j0 * p.ldw;
-    d.lda = p.ldw;
-    d.a_row = 0;
-    d.a_conj = 0;
-    d.a_mask = MASK_UNIT_LOWER;
-    d.B = p.Z;
-    d.ldb = kb;
-    d.C = Q + j0 + (int64_t)j0 * ldq;
-    d.ldc = ldq;
-    CK(gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s));
-    hook_after(hooks, K(MPS_KCLASS_FORMQ), 2 + nl);
+    int nl = 0;
+    hook_before(hooks, K(MPS_KCLASS_FORMQ), (2.0 * M * N + 2.0 * M * kbb) * sizeof(T), 16.0 * M * N * kbb);
+    CK(apply_block<T>(p, j0, kbb, p.Tblk + (size_t)bi * ob * ob, ob, 0, Q, ldq, j0, N, &nl, s));
+    hook_after(hooks, K(MPS_KCLASS_FORMQ), nl);
   }
   return cudaSuccess;
 }
