@@ -150,6 +150,64 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, i
   return s_ok != 0;
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok;
+}
+// Bounded wait for the phase of the given parity; false (and the error word set)
+// on expiry or when another thread has already failed.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, unsigned long long timeout_ns) {
+  if (mbar_try(a, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 255u) == 0u) {
+      if (ld_relaxed_i32(err) != DEV_OK) return false;
+      if (globaltimer_ns() - t0 > timeout_ns) {
+        atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// Bounded wait that ignores the error word: lets an asynchronous copy that is
+// already in flight land before its buffer is reused or the CTA leaves.
+__device__ __forceinline__ bool mbar_wait_plain(uint32_t a, uint32_t parity, unsigned long long timeout_ns) {
+  if (mbar_try(a, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 255u) == 0u && globaltimer_ns() - t0 > timeout_ns) return false;
+  }
+}
+// Arrive on the barrier and add `bytes` to the transaction count of its phase.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+// Bulk asynchronous copy global -> shared (TMA, untiled): src and dst 16-byte
+// aligned, bytes a multiple of 16; completion is signalled on `mbar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+// Order this thread's generic-proxy accesses with later async-proxy ones.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll

@@ -47,6 +47,9 @@ constexpr int PNW = PNT / 32;
 constexpr int kPanelNbMax = 32;  // widest panel the kernel supports
 constexpr int kDBatch = 32;      // trailing columns per phase-D batch
 constexpr int kDChMax = 32;      // row chunks per column in phase D (about 8 KB each)
+constexpr int kDpCap = kDBatch * kDChMax;  // phase-D chunk sums held at once
+constexpr int kSlot = 4096;      // bytes of one bulk-copy slot (phase D, bulk mode)
+constexpr int kRing = PNW * 2 * kSlot;  // two slots per warp
 
 template <typename T>
 struct PanelArgs {
@@ -72,7 +75,9 @@ struct PanelArgs {
   unsigned expected;
   unsigned long long timeout_ns;
   double flag_tol;
-  int xcap;  // elements of x that fit in dynamic shared memory
+  int xcap;    // elements of x that fit in dynamic shared memory
+  int xs_off;  // byte offset of the x vector in dynamic shared memory
+  int bulk;    // phase D streams column chunks with bulk asynchronous copies
 };
 
 // Pivot key of a squared norm: for a non-negative double (or +inf) its bit
@@ -245,15 +250,69 @@ __device__ __forceinline__ c128 warp_dot_conj<c128>(const c128* __restrict__ col
   return s;
 }
 
+// y = sum_r conj(c[r]) x[r] over one column chunk held in shared memory (c)
+// and x in shared or global memory; rows [0, nrows), row 0 left out when
+// skip0.  Result warp-reduced (every lane).  For complex64 nrows is even and
+// both pointers 16-byte aligned.
+template <typename T>
+__device__ __forceinline__ T chunk_dot(const T* c, const T* x, int nrows, bool skip0, int lane);
+
+template <>
+__device__ __forceinline__ c64 chunk_dot<c64>(const c64* c, const c64* x, int nrows, bool skip0, int lane) {
+  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const int nq = nrows >> 1;
+#pragma unroll 4
+  for (int q = lane; q < nq; q += 32) {
+    float4 v = c4[q];
+    const float4 xv = x4[q];
+    if (q == 0 && skip0) {
+      v.x = 0.f;
+      v.y = 0.f;
+    }
+    dot_pair(v, xv, ar, ai, br, bi);
+  }
+  c64 s;
+  s.re = warp_sum(ar + br);
+  s.im = warp_sum(ai + bi);
+  return s;
+}
+
+template <>
+__device__ __forceinline__ c128 chunk_dot<c128>(const c128* c, const c128* x, int nrows, bool skip0, int lane) {
+  double ar = 0.0, ai = 0.0;
+  const double2* c2 = reinterpret_cast<const double2*>(c);
+  const double2* x2 = reinterpret_cast<const double2*>(x);
+#pragma unroll 4
+  for (int r = lane; r < nrows; r += 32) {
+    double2 v = c2[r];
+    const double2 xv = x2[r];
+    if (r == 0 && skip0) {
+      v.x = 0.0;
+      v.y = 0.0;
+    }
+    ar = fma(v.x, xv.x, ar);
+    ar = fma(v.y, xv.y, ar);
+    ai = fma(v.x, xv.y, ai);
+    ai = fma(-v.y, xv.x, ai);
+  }
+  c128 s;
+  s.re = warp_sum(ar);
+  s.im = warp_sum(ai);
+  return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   using R = typename real_of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);
+  T* xs = reinterpret_cast<T*>(smem_raw + a.xs_off);
+  __shared__ __align__(8) unsigned long long s_mbar[PNW][2];  // bulk mode: one barrier per slot
   __shared__ T s_w[kPanelNbMax];      // w_i = V_i^H v
   __shared__ T s_vrow[kPanelNbMax];   // W[J, j0+i]
   __shared__ T s_wp[PNW][kPanelNbMax];  // per-warp partials of V^H x (phase B)
-  __shared__ T s_dp[kDBatch * kDChMax];  // phase-D chunk sums
+  __shared__ T s_dp[kDpCap];  // phase-D chunk sums
   __shared__ int s_bi;
   __shared__ c128 s_scal[3];  // tau, 1/(alpha-beta), beta
 
@@ -266,6 +325,11 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   // (decided once for the whole CTA)
   __shared__ int s_skip;
   if (tid == 0) s_skip = ld_relaxed_i32(a.err) != DEV_OK;
+  if (a.bulk && lane == 0) {
+    mbar_init(smem_u32(&s_mbar[warp][0]), 1);
+    mbar_init(smem_u32(&s_mbar[warp][1]), 1);
+  }
+  unsigned ph = 0;  // bulk mode: parity of the next completion of this warp's slots
   __syncthreads();
   if (s_skip) return;
 
@@ -434,6 +498,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       a.jpvt[J] = a.jpvt[p];
       a.jpvt[p] = t0;
     }
+    if (a.bulk) fence_proxy_async();  // phase-B writes (column swap) before later bulk reads
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
 
     // ---------------- C: reflector (every CTA, identical FP64 arithmetic)
@@ -535,17 +600,61 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     split_range(J + 1, a.nend, G, b, c0, c1);
     long long bv = -1;
     int bi = 0x7fffffff;
-    for (int cb = c0; cb < c1; cb += kDBatch) {
-      const int nc = min(kDBatch, c1 - cb);
+    // bulk mode: chunks of kSlot bytes from row xbase, each copied by the TMA
+    // unit into one of the consuming warp's two slots (double buffering)
+    constexpr int CR = kSlot / (int)sizeof(T);
+    const int nchb = a.bulk ? (Lx + CR - 1) / CR : nch;  // chunks per column
+    const int nbc = a.bulk ? max(1, min(kDBatch, kDpCap / max(nchb, 1))) : kDBatch;
+    if (a.bulk && lane == 0) fence_proxy_async();  // generic writes before the barrier -> async reads
+    for (int cb = c0; cb < c1; cb += nbc) {
+      const int nc = min(nbc, c1 - cb);
       // D1: chunk sums
-      for (int it = warp; it < nc * nch; it += PNW) {
-        const int cl = it / nch, ch = it - cl * nch;
-        const int t = cb + cl;
-        const int r0 = max(J + 1, xbase + ch * chr), r1 = min(m, xbase + (ch + 1) * chr);
-        const T* col = W + (int64_t)t * ldw;
-        T s = mk<R>(0, 0);
-        if (r0 < r1) s = warp_dot_conj<T>(col, xsrc, xbase, r0, r1, lane);
-        if (lane == 0) s_dp[cl * kDChMax + ch] = s;
+      if (a.bulk) {
+        const int nit = nc * nchb;
+        const int nli = nit > warp ? (nit - warp + PNW - 1) / PNW : 0;  // this warp's items
+        unsigned char* slot0 = smem_raw + warp * 2 * kSlot;
+        if (lane == 0) {
+          for (int li = 0; li < min(2, nli); ++li) {
+            const int it = warp + PNW * li, cl = it / nchb, ch = it - cl * nchb;
+            const int cs = xbase + ch * CR, ce = min(m, cs + CR);
+            const uint32_t mb = smem_u32(&s_mbar[warp][li]);
+            mbar_expect_tx(mb, (uint32_t)((ce - cs) * sizeof(T)));
+            bulk_g2s(smem_u32(slot0 + li * kSlot), W + (int64_t)(cb + cl) * ldw + cs, (uint32_t)((ce - cs) * sizeof(T)),
+                     mb);
+          }
+        }
+        for (int li = 0; li < nli; ++li) {
+          const int q = li & 1;
+          const int it = warp + PNW * li, cl = it / nchb, ch = it - cl * nchb;
+          const int cs = xbase + ch * CR, ce = min(m, cs + CR);
+          const uint32_t mb = smem_u32(&s_mbar[warp][q]);
+          const uint32_t par = (ph >> q) & 1u;
+          // on expiry (error word set) the copy in flight still lands before the slot is reused
+          if (!mbar_wait(mb, par, a.err, a.timeout_ns)) mbar_wait_plain(mb, par, a.timeout_ns);
+          ph ^= 1u << q;
+          const T s = chunk_dot<T>(reinterpret_cast<const T*>(slot0 + q * kSlot), xsrc + (cs - xbase), ce - cs,
+                                   cs <= J, lane);
+          if (lane == 0) s_dp[cl * nchb + ch] = s;
+          __syncwarp();
+          if (lane == 0 && li + 2 < nli) {
+            const int it2 = it + 2 * PNW, cl2 = it2 / nchb, ch2 = it2 - cl2 * nchb;
+            const int cs2 = xbase + ch2 * CR, ce2 = min(m, cs2 + CR);
+            fence_proxy_async();  // this slot's reads before the next asynchronous write into it
+            mbar_expect_tx(mb, (uint32_t)((ce2 - cs2) * sizeof(T)));
+            bulk_g2s(smem_u32(slot0 + q * kSlot), W + (int64_t)(cb + cl2) * ldw + cs2,
+                     (uint32_t)((ce2 - cs2) * sizeof(T)), mb);
+          }
+        }
+      } else {
+        for (int it = warp; it < nc * nch; it += PNW) {
+          const int cl = it / nch, ch = it - cl * nch;
+          const int t = cb + cl;
+          const int r0 = max(J + 1, xbase + ch * chr), r1 = min(m, xbase + (ch + 1) * chr);
+          const T* col = W + (int64_t)t * ldw;
+          T s = mk<R>(0, 0);
+          if (r0 < r1) s = warp_dot_conj<T>(col, xsrc, xbase, r0, r1, lane);
+          if (lane == 0) s_dp[cl * nch + ch] = s;
+        }
       }
       __syncthreads();
       // D2: per-column epilogue; operands of all of this warp's columns fetched first
@@ -580,7 +689,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         const T* Fs = a.F + (int64_t)src * nb;
         T* Ft = a.F + (int64_t)t * nb;
         T acc = mk<R>(0, 0);
-        for (int ch = 0; ch < nch; ++ch) acc = acc + s_dp[cl * kDChMax + ch];
+        for (int ch = 0; ch < nchb; ++ch) acc = acc + s_dp[cl * nchb + ch];
         const T wJt = wJtT[q];
         const T y = cconj(wJt) + sc * acc;
         // F[t, kk] = tau * (y - sum_i F[src, i] w_i); row update of W[J, t]
@@ -657,6 +766,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       }
     }
     s_prev = s_scal[1];
+    if (a.bulk) fence_proxy_async();  // this step's generic writes before later bulk reads
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
   }
   // final deferred scaling of the panel's last reflector, rows > Jl
@@ -841,11 +951,6 @@ int num_sms() {
 }
 
 constexpr int kPanelSmem = 200 * 1024;  // dynamic shared memory of the panel kernel
-
-template <typename T>
-static int panel_xcap(int) {
-  return kPanelSmem / (int)sizeof(T);
-}
 
 template <typename T>
 static cudaError_t panel_setup(int& max_blocks) {
@@ -1056,7 +1161,10 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     a.err = p.err;
     a.timeout_ns = p.timeout_ns;
     a.flag_tol = p.flag_tol;
-    a.xcap = panel_xcap<T>(nb);
+    // bulk copies need 16-byte aligned column chunks: an aligned base, a
+    // 16-byte multiple column stride and (complex64) chunks of whole row pairs
+    a.bulk = (reinterpret_cast<uintptr_t>(p.W) % 16 == 0) && ((p.ldw * (int64_t)sizeof(T)) % 16 == 0) &&
+             (sizeof(T) == 16 || m % 2 == 0);
     const int ncols = a.nend - j0;
     // enough CTAs for both the per-step row work (phase B) and the trailing columns
     int G = std::max(1, std::min(gcap, std::max((ncols + 7) / 8, (m - j0 + 63) / 64)));
@@ -1068,12 +1176,24 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       bytes += rows * cols * sizeof(T);
       flops += 8.0 * rows * cols;
     }
-    // dynamic shared memory sized to the x vector this panel stages (rounded to
-    // 16 KB): the rest of the SM's unified L1/shared storage stays L1, which
-    // holds the trailing sweep's loads in flight
-    const int need = (int)std::min<int64_t>((int64_t)(m - j0 + 2) * sizeof(T), smem);
-    const int dyn = std::min(smem, (need + 16383) / 16384 * 16384);
-    a.xcap = dyn / (int)sizeof(T);
+    int dyn;
+    if (a.bulk) {
+      // bulk mode: the copy slots, then x when it fits beside them (else x is
+      // read from global memory, where it stays in L2)
+      const int64_t xb = ((int64_t)(m - j0 + 2) * sizeof(T) + 15) / 16 * 16;
+      const bool fits = kRing + xb <= smem;
+      dyn = kRing + (fits ? (int)xb : 0);
+      a.xs_off = kRing;
+      a.xcap = fits ? (int)(xb / (int64_t)sizeof(T)) : 0;
+    } else {
+      // dynamic shared memory sized to the x vector this panel stages (rounded
+      // to 16 KB): the rest of the SM's unified L1/shared storage stays L1,
+      // which holds the trailing sweep's loads in flight
+      const int need = (int)std::min<int64_t>((int64_t)(m - j0 + 2) * sizeof(T), smem);
+      dyn = std::min(smem, (need + 16383) / 16384 * 16384);
+      a.xs_off = 0;
+      a.xcap = dyn / (int)sizeof(T);
+    }
     void* args[] = {&a};
     hook_before(hooks, K(MPS_KCLASS_PANEL), bytes, flops);
     CK(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<T>, dim3(G), dim3(PNT), args, (size_t)dyn, s));

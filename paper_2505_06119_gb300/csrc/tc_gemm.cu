@@ -66,40 +66,6 @@ struct TcArgs {
   unsigned long long timeout_ns;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ uint32_t mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok;
-}
-// Bounded wait for the phase of the given parity; false (and the error word set)
-// on expiry or when another thread has already failed.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, unsigned long long timeout_ns) {
-  if (mbar_try(a, parity)) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try(a, parity)) return true;
-    if ((it & 255u) == 0u) {
-      if (ld_relaxed_i32(err) != DEV_OK) return false;
-      if (globaltimer_ns() - t0 > timeout_ns) {
-        atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
 // 1024 bytes (stride byte offset), SM100 descriptor version 1.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
