@@ -43,6 +43,7 @@ int max_bond(int n, int b, int chi) {
 struct WsLayout {
   size_t W, Q, F, vn1, vn2, jpvt, inv, tau, Tfac, Wg, Tblk, G12, Y, Z, SK, red_norm, red_w, red_argv, red_argi, alpha,
       bar, err, disc, total;
+  int64_t sk_elems;
 };
 
 WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int64_t& ldw, int64_t& ldq) {
@@ -71,7 +72,8 @@ WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int6
   L.G12 = take(esz * (size_t)nb * nb);
   L.Y = take(esz * (size_t)2 * nb * std::max(wide, 1));
   L.Z = take(esz * (size_t)2 * nb * std::max(wide, 1));
-  L.SK = take(esz * (size_t)kMaxSplit * 2 * nb * std::max(wide, 1));
+  L.sk_elems = (int64_t)kMaxSplit * 2 * nb * std::max(wide, 1);
+  L.SK = take(esz * (size_t)L.sk_elems);
   L.red_norm = take(8 * (size_t)G);
   L.red_w = take(16 * (size_t)G * nb);
   L.red_argv = take(8 * (size_t)G);
@@ -103,6 +105,7 @@ struct Ws {
   T* Y;
   T* Z;
   T* SK;
+  int64_t sk_cap;
   double* red_norm;
   c128* red_w;
   double* red_argv;
@@ -133,6 +136,7 @@ Ws<T> ws_views(char* base, const WsLayout& L, int64_t ldw, int64_t ldq) {
   w.Y = (T*)(base + L.Y);
   w.Z = (T*)(base + L.Z);
   w.SK = (T*)(base + L.SK);
+  w.sk_cap = L.sk_elems;
   w.red_norm = (double*)(base + L.red_norm);
   w.red_w = (c128*)(base + L.red_w);
   w.red_argv = (double*)(base + L.red_argv);
@@ -185,6 +189,7 @@ QrPlan<T> make_plan(const Ws<T>& w, const Knobs& kn, int m, int n, int k, int pi
   p.Y = w.Y;
   p.Z = w.Z;
   p.SK = w.SK;
+  p.sk_cap = w.sk_cap;
   p.G = kn.G;
   p.flag_tol = kn.flag_tol;
   p.timeout_ns = kn.timeout_ns;

@@ -1,7 +1,8 @@
-// Complex GEMMs on the CUDA cores (FP64 DFMA for complex128, FP32 FFMA for
-// complex64): the generic GEMM used by the block-reflector updates, centre
-// moves and contractions, and the theta contraction with its fused gate
-// epilogue (Sec. III-B.1 bond contraction, Sec. III-C.2 tensor application).
+// Complex GEMMs on the CUDA cores: the generic GEMM used by the block-reflector
+// updates, centre moves and contractions, and the theta contraction with its
+// fused gate epilogue (Sec. III-B.1 bond contraction, Sec. III-C.2 tensor
+// application).  The kernels here serve complex128 (FP64 DFMA); complex64
+// products go to the wider-tile kernels of gemm_c64.cu.
 #include <algorithm>
 #include <type_traits>
 
@@ -160,115 +161,6 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmDesc<T> d) {
   }
 }
 
-// complex64 variant with a 128 x 64 tile: each thread owns rows
-// {4tm..4tm+3} and {64+4tm..64+4tm+3} and columns {4tn..4tn+3} (32 complex
-// accumulators), so every shared-memory float read feeds 5.3 FMAs.
-constexpr int BM2 = 128;
-
-__global__ void __launch_bounds__(NT) gemm_simt_c64_big_kernel(GemmDesc<c64> d) {
-  __shared__ __align__(16) c64 As[2][BK][BM2];
-  __shared__ __align__(16) c64 Bs[2][BK][BN];
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * BM2, j0 = blockIdx.y * BN;
-  int kbeg = 0, kend = d.K;
-  if (d.splitk > 1) {
-    int per = ((d.K + d.splitk - 1) / d.splitk + BK - 1) / BK * BK;
-    kbeg = blockIdx.z * per;
-    kend = min(d.K, kbeg + per);
-  }
-  const int tm = tid % 16, tn = tid / 16;
-  // global->smem mapping: 4 elements of A (128 x 8) and 2 of B (8 x 64) per thread
-  int ai[4], ak[4], bk[2], bj[2];
-  for (int e = 0; e < 4; ++e) {
-    int t = tid + e * NT;  // 0..1023
-    if (d.a_row) {
-      ai[e] = t / BK;
-      ak[e] = t % BK;
-    } else {
-      ai[e] = t % BM2;
-      ak[e] = t / BM2;
-    }
-  }
-  for (int e = 0; e < 2; ++e) {
-    int t = tid + e * NT;
-    if (d.b_row) {
-      bj[e] = t % BN;
-      bk[e] = t / BN;
-    } else {
-      bj[e] = t / BK;
-      bk[e] = t % BK;
-    }
-  }
-  c64 acc[8][4];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = mk<float>(0.f, 0.f);
-  c64 ra[4], rb[2];
-  const int nslices = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
-  for (int e = 0; e < 4; ++e) ra[e] = load_a(d, i0 + ai[e], kbeg + ak[e], kend);
-  for (int e = 0; e < 2; ++e) rb[e] = load_b(d, kbeg + bk[e], j0 + bj[e], kend);
-  for (int e = 0; e < 4; ++e) As[0][ak[e]][ai[e]] = ra[e];
-  for (int e = 0; e < 2; ++e) Bs[0][bk[e]][bj[e]] = rb[e];
-  __syncthreads();
-  for (int s = 0; s < nslices; ++s) {
-    const int buf = s & 1;
-    if (s + 1 < nslices) {
-      const int kb = kbeg + (s + 1) * BK;
-      for (int e = 0; e < 4; ++e) ra[e] = load_a(d, i0 + ai[e], kb + ak[e], kend);
-      for (int e = 0; e < 2; ++e) rb[e] = load_b(d, kb + bk[e], j0 + bj[e], kend);
-    }
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      c64 av[8], bv[4];
-      const float4* pa0 = reinterpret_cast<const float4*>(&As[buf][kk][tm * 4]);
-      const float4* pa1 = reinterpret_cast<const float4*>(&As[buf][kk][64 + tm * 4]);
-      const float4* pb = reinterpret_cast<const float4*>(&Bs[buf][kk][tn * 4]);
-      float4 q0 = pa0[0], q1 = pa0[1], q2 = pa1[0], q3 = pa1[1], q4 = pb[0], q5 = pb[1];
-      av[0] = mk<float>(q0.x, q0.y);
-      av[1] = mk<float>(q0.z, q0.w);
-      av[2] = mk<float>(q1.x, q1.y);
-      av[3] = mk<float>(q1.z, q1.w);
-      av[4] = mk<float>(q2.x, q2.y);
-      av[5] = mk<float>(q2.z, q2.w);
-      av[6] = mk<float>(q3.x, q3.y);
-      av[7] = mk<float>(q3.z, q3.w);
-      bv[0] = mk<float>(q4.x, q4.y);
-      bv[1] = mk<float>(q4.z, q4.w);
-      bv[2] = mk<float>(q5.x, q5.y);
-      bv[3] = mk<float>(q5.z, q5.w);
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
-    }
-    if (s + 1 < nslices) {
-      for (int e = 0; e < 4; ++e) As[buf ^ 1][ak[e]][ai[e]] = ra[e];
-      for (int e = 0; e < 2; ++e) Bs[buf ^ 1][bk[e]][bj[e]] = rb[e];
-    }
-    __syncthreads();
-  }
-  const bool beta_zero = (d.beta.re == 0.f && d.beta.im == 0.f);
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const int j = j0 + tn * 4 + b;
-    if (j >= d.N) continue;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int i = i0 + (a < 4 ? tm * 4 + a : 64 + tm * 4 + (a - 4));
-      if (i >= d.M) continue;
-      if (d.splitk > 1) {
-        d.wk[(int64_t)blockIdx.z * d.M * d.N + i + (int64_t)j * d.M] = acc[a][b];
-      } else {
-        c64* c = d.C + i + (int64_t)j * d.ldc;
-        c64 v = d.alpha * acc[a][b];
-        if (!beta_zero) v = v + d.beta * (*c);
-        *c = v;
-      }
-    }
-  }
-}
-
 // C = alpha * sum_z P[z] + beta * C, summed in z order
 template <typename T>
 __global__ void splitk_reduce_kernel(GemmDesc<T> d) {
@@ -413,12 +305,14 @@ __global__ void __launch_bounds__(NT) theta_kernel(ThetaArgs<T> p) {
 
 }  // namespace
 
-int choose_splitk(int M, int N, int K, int max_split) {
-  int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  int want = (2 * 152 + tiles - 1) / tiles;
-  int by_k = K / 256;
-  int s = std::min(std::min(want, by_k), max_split);
-  return s < 1 ? 1 : s;
+int choose_splitk(int M, int N, int K, int64_t cap_elems, int elem_bytes) {
+  const int bm = elem_bytes == 8 ? gemm_c64_tile_rows(M, K) : BM, bn = elem_bytes == 8 ? 128 : BN;
+  const int64_t tiles = (int64_t)((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+  const int64_t want = (2 * 152 + tiles - 1) / tiles;
+  const int64_t by_k = K / 64;
+  const int64_t by_cap = cap_elems / std::max<int64_t>(1, (int64_t)M * N);
+  const int64_t s = std::min(std::min(want, by_k), std::min<int64_t>(by_cap, 256));
+  return s < 1 ? 1 : (int)s;
 }
 
 template <typename T>
@@ -427,22 +321,15 @@ cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s) {
   const int sk = (d.splitk > 1 && d.wk) ? d.splitk : 1;
   GemmDesc<T> dd = d;
   dd.splitk = sk;
+  cudaError_t e;
   if constexpr (std::is_same<T, c64>::value) {
-    if (d.M >= 96 && d.K >= 256) {  // long contractions: the 128-row tile pays off
-      dim3 grid((d.M + BM2 - 1) / BM2, (d.N + BN - 1) / BN, sk);
-      if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-      gemm_simt_c64_big_kernel<<<grid, NT, 0, s>>>(dd);
-    } else {
-      dim3 grid((d.M + BM - 1) / BM, (d.N + BN - 1) / BN, sk);
-      if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-      gemm_simt_kernel<T><<<grid, NT, 0, s>>>(dd);
-    }
+    e = gemm_c64(dd, s);
   } else {
     dim3 grid((d.M + BM - 1) / BM, (d.N + BN - 1) / BN, sk);
     if (grid.y > 65535) return cudaErrorInvalidConfiguration;
     gemm_simt_kernel<T><<<grid, NT, 0, s>>>(dd);
+    e = cudaGetLastError();
   }
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || sk == 1) return e;
   int64_t total = (int64_t)d.M * d.N;
   splitk_reduce_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dd);
@@ -452,6 +339,7 @@ cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s) {
 template <typename T>
 cudaError_t theta_gemm_simt(int chi_l, int chi_m, int chi_r, const T* A, const T* B, const T* g16,
                             T* W, int64_t ldw, cudaStream_t s) {
+  if constexpr (std::is_same<T, c64>::value) return theta_c64(chi_l, chi_m, chi_r, A, B, g16, W, ldw, s);
   ThetaArgs<T> p;
   p.cl = chi_l;
   p.cm = chi_m;

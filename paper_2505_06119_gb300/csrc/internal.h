@@ -47,8 +47,17 @@ template <typename T>
 int gemm_launches(const GemmDesc<T>& d) {
   return d.splitk > 1 ? 2 : 1;
 }
-// split count that fills the GPU for a skinny product (few output tiles, long K)
-int choose_splitk(int M, int N, int K, int max_split);
+// split count that fills the GPU for a skinny product (few output tiles, long
+// K), at most cap_elems / (M N) so the partials fit the workspace
+int choose_splitk(int M, int N, int K, int64_t cap_elems, int elem_bytes);
+
+// complex64 GEMM kernels (gemm_c64.cu): same operand views and split-K
+// protocol as gemm_simt (the caller runs the reduction); theta contraction
+// with the gate epilogue
+cudaError_t gemm_c64(const GemmDesc<c64>& d, cudaStream_t s);
+cudaError_t theta_c64(int cl, int cm, int cr, const c64* A, const c64* B, const c64* g16, c64* W, int64_t ldw,
+                      cudaStream_t s);
+int gemm_c64_tile_rows(int M, int K);
 
 // Tensor-core (tcgen05, 3xTF32) complex64 GEMM with the same operand views
 // as gemm_simt (no split-K); a wait that expires sets *err.
@@ -134,6 +143,7 @@ struct QrPlan {
   T* Y;               // 2nb * max(n, k) scratch for block-reflector GEMMs
   T* Z;               // 2nb * max(n, k)
   T* SK;              // split-K partials: kMaxSplit * 2nb * max(n, k)
+  int64_t sk_cap = 0; // elements of SK
   int G;              // cooperative grid size cap
   double flag_tol;    // norm-downdate recompute threshold
   unsigned long long timeout_ns;

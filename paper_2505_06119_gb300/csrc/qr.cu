@@ -781,34 +781,45 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
 }
 
 // Triangular factor of each panel's block reflector (H_j0 ... H_j0+kb-1 =
-// I - V T V^H, forward columnwise): T[kk, kk] = tau_kk and
-// T[0:kk, kk] = -tau_kk T[0:kk, 0:kk] w_kk with w_kk = V[:, 0:kk]^H v_kk saved by
-// the panel kernel.  One CTA per panel, FP64.
+// I - V T V^H, forward columnwise), built by recursive doubling: the factor
+// of [V1 V2] is [[T1, -T1 (V1^H V2) T2], [0, T2]], so starting from the
+// 1 x 1 factors tau_i, log2(nb) rounds merge neighbouring blocks of width h
+// into blocks of width 2h.  The Gram entries V_j^H v_i (j < i) are the w
+// vectors the panel kernel saved (FP64); the arithmetic runs in the data
+// precision.  One CTA of 1024 threads per panel, thread (i, j) owns T[i, j].
 template <typename T>
-__global__ void tfactor_kernel(const c128* Wg, const T* tau, int pan0, int k, int nb, T* Tfac) {
+__global__ void __launch_bounds__(1024) tfactor_kernel(const c128* Wg, const T* tau, int pan0, int k, int nb,
+                                                       T* Tfac) {
   using R = typename real_of<T>::type;
-  __shared__ c128 Ts[kPanelNbMax * kPanelNbMax];
+  __shared__ T Ts[kPanelNbMax][kPanelNbMax + 1];
+  __shared__ T Gs[kPanelNbMax][kPanelNbMax + 1];
   const int pan = pan0 + blockIdx.x;
   const int j0 = pan * nb, kb = min(nb, k - j0);
   const c128* w = Wg + (size_t)pan * nb * nb;
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) Ts[e] = mk<double>(0, 0);
+  const int i = threadIdx.x % 32, j = threadIdx.x / 32;
+  const T z = mk<R>(0, 0);
+  Ts[i][j] = (i == j && i < kb) ? tau[j0 + i] : z;
+  Gs[i][j] = (i < j && j < kb) ? ccast<R>(w[(size_t)j * nb + i]) : z;  // V_i^H v_j
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int kk = 0; kk < kb; ++kk) {
-      const c128 t = ccast<double>(tau[j0 + kk]);
-      for (int i = lane; i < kk; i += 32) {
-        c128 acc = mk<double>(0, 0);
-        for (int j = i; j < kk; ++j) cfma(acc, Ts[i + j * nb], w[(size_t)kk * nb + j]);
-        Ts[i + kk * nb] = mk<double>(0, 0) - t * acc;
-      }
-      if (lane == 0) Ts[kk + kk * nb] = t;
-      __syncwarp();
+  for (int h = 1; h < kb; h *= 2) {
+    const int s0 = i / (2 * h) * (2 * h);
+    const bool mine = (j / (2 * h) == i / (2 * h)) && (i - s0 < h) && (j - s0 >= h);
+    // X = T1 G12 into the (still empty) upper-right block
+    if (mine) {
+      T x = z;
+      for (int l = i; l < s0 + h; ++l) cfma(x, Ts[i][l], Gs[l][j]);
+      Ts[i][j] = x;
     }
+    __syncthreads();
+    // T12 = -X T2
+    T y = z;
+    if (mine)
+      for (int l = s0 + h; l <= j; ++l) cfma(y, Ts[i][l], Ts[l][j]);
+    __syncthreads();
+    if (mine) Ts[i][j] = z - y;
+    __syncthreads();
   }
-  __syncthreads();
-  T* out = Tfac + (size_t)pan * nb * nb;
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) out[e] = ccast<R>(Ts[e]);
+  if (i < nb && j < nb) Tfac[(size_t)pan * nb * nb + i + (size_t)j * nb] = Ts[i][j];
 }
 
 // Squared norm of col[r0:r1) by one warp.  complex128: FP64 throughout.
@@ -1016,7 +1027,7 @@ static cudaError_t outer_tfactor(const QrPlan<T>& p, int pi, int* kbb_out, int* 
     d.b_mask = MASK_UNIT_LOWER;
     d.C = p.G12;
     d.ldc = nb;
-    d.splitk = choose_splitk(k1, k2, d.K, kMaxSplit);
+    d.splitk = choose_splitk(k1, k2, d.K, p.sk_cap, (int)sizeof(T));
     d.wk = p.SK;
     *nl += gemm_launches(d);
     CK(gemm_simt<T>(d, s));
@@ -1055,7 +1066,7 @@ static cudaError_t apply_block(const QrPlan<T>& p, int j0, int kbb, const T* Tb,
   d.b_mask = MASK_NONE;
   d.C = p.Y;
   d.ldc = kbb;
-  d.splitk = choose_splitk(kbb, N, M, kMaxSplit);
+  d.splitk = choose_splitk(kbb, N, M, p.sk_cap, (int)sizeof(T));
   d.wk = p.SK;
   *nl += gemm_launches(d);
   CK(gemm_simt<T>(d, s));
@@ -1244,7 +1255,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
       const int c1 = first_of_pair ? std::min(k, j0 + 2 * nb) : n;  // partner columns only
       const double M = m - jb, N = c1 - c0, kr = first_of_pair ? kb : c0 - jb;
       hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * kr + 3.0 * M * N) * sizeof(T), 16.0 * M * N * kr);
-      tfactor_kernel<T><<<1, 128, 0, s>>>(p.Wg, p.tau, pi, k, nb, p.Tfac);
+      tfactor_kernel<T><<<1, 1024, 0, s>>>(p.Wg, p.tau, pi, k, nb, p.Tfac);
       CK(cudaGetLastError());
       if (first_of_pair) {
         CK(apply_block<T>(p, j0, kb, p.Tfac + (size_t)pi * nb * nb, nb, 1, p.W, p.ldw, c0, c1 - c0, &nl, s));
@@ -1265,7 +1276,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     const int cnt = p.pivot ? npanels : 1;
     int nl = 1;
     hook_before(hooks, K(MPS_KCLASS_FORMQ), 0, 0);
-    tfactor_kernel<T><<<cnt, 128, 0, s>>>(p.Wg, p.tau, first, k, nb, p.Tfac);
+    tfactor_kernel<T><<<cnt, 1024, 0, s>>>(p.Wg, p.tau, first, k, nb, p.Tfac);
     CK(cudaGetLastError());
     for (int pb = 2 * tblk_done; pb < npanels; pb += 2) {
       int kbb = 0;
