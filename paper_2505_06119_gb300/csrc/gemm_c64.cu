@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
     cp_async_commit();
     const c64* Ab = As + (s % kStages) * G_BK * LAS + 2 * tm;
     const c64* Bb = Bs + (s % kStages) * G_BK * LBS + 2 * tn;
-#pragma unroll
+    // partially unrolled: a fully unrolled slice overflows the instruction cache
+#pragma unroll 4
     for (int kk = 0; kk < G_BK; ++kk) {
       float4 av[RG], bv[4];
 #pragma unroll

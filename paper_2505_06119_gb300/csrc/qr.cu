@@ -780,6 +780,224 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Unpivoted panel on one thread-block cluster (centre moves, Sec. III-C.1).
+// The panel W[j0:m, j0:j0+kb] is spread over the cluster's CTAs by rows and
+// stays in their shared memory for the whole factorisation; each step needs
+// two cluster-wide reductions (the reflector norm with alpha, then v^H of
+// every panel column), exchanged through distributed shared memory between
+// hardware cluster barriers instead of grid barriers in global memory.
+// Per step J = j0 + kk (right-looking inside the panel):
+//   beta = -sign(Re alpha) ||x||, tau = (beta - alpha)/beta, v = (1, x/(alpha-beta))
+//   d_c = v^H W[J:m, c] for every panel column c;
+//   c > kk: W[J:m, c] -= conj(tau) v d_c;   c < kk: w_kk[c] = conj(d_c) (T factor)
+// Control flow is identical in every CTA (no early exit), so every cluster
+// barrier is reached by all of them; FP64 carries the norm, beta and tau.
+constexpr int CPT = 512;             // threads of the cluster panel kernel
+constexpr int CPW = CPT / 32;
+constexpr int kClusterMax = 16;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t map_cta(const void* p, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double ld_dsmem_f64(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ c64 ld_dsmem(const c64*, uint32_t a) {
+  float x, y;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a) : "memory");
+  return mk<float>(x, y);
+}
+__device__ __forceinline__ c128 ld_dsmem(const c128*, uint32_t a) {
+  double x, y;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a) : "memory");
+  return mk<double>(x, y);
+}
+
+template <typename T>
+struct CPanelArgs {
+  T* W;
+  int64_t ldw;
+  int m, j0, kb, nb;
+  int rb;        // panel rows held by each CTA
+  T* tau;
+  c128* Wg;      // this panel's w vectors (column kk = w of step kk)
+};
+
+// Block-wide FP64 sum; the result is returned to every thread of warp 0.
+__device__ __forceinline__ double cp_block_sum(double v, double* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < CPW ? s_red[lane] : 0.0;
+    for (int o = 1; o < CPW; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
+  using R = typename real_of<T>::type;
+  extern __shared__ __align__(16) unsigned char cp_raw[];
+  T* P = reinterpret_cast<T*>(cp_raw);  // [kb][rb], column c at P + c * rb
+  __shared__ double s_r1[2][3];          // per step: ||x_{J+1:}||^2 partial, alpha (re, im)
+  __shared__ T s_r2[2][kPanelNbMax];     // per step: partial v^H W[:, c]
+  __shared__ T s_f[kPanelNbMax];         // conj(tau) d_c
+  __shared__ T s_d[kPanelNbMax];         // reduced d_c
+  __shared__ double s_red[CPW];
+  __shared__ c128 s_sc[3];               // tau, 1/(alpha-beta), beta
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned cs = gridDim.x;          // CTAs in the cluster (one cluster)
+  const unsigned rank = cluster_rank();
+  const int m = a.m, kb = a.kb, rb = a.rb;
+  const int r0 = a.j0 + (int)rank * rb, r1 = min(m, r0 + rb);
+  const int nr = max(0, r1 - r0);
+  // this CTA's contribution to the norm of column c below row J, and alpha = W[J, c]
+  auto norm_partial = [&](int c, int J, double part) {
+    const double t = cp_block_sum(part, s_red);
+    if (tid == 0) {
+      const bool own = J >= r0 && J < r1;
+      const T al = own ? P[c * rb + (J - r0)] : mk<R>(0, 0);
+      s_r1[c & 1][0] = t;
+      s_r1[c & 1][1] = (double)al.re;
+      s_r1[c & 1][2] = (double)al.im;
+    }
+  };
+  for (int c = 0; c < kb; ++c)
+    for (int rr = tid; rr < nr; rr += CPT) P[c * rb + rr] = a.W[(r0 + rr) + (int64_t)(a.j0 + c) * a.ldw];
+  __syncthreads();
+  {
+    double part = 0.0;
+    for (int rr = max(0, a.j0 + 1 - r0) + tid; rr < nr; rr += CPT) {
+      const T v = P[rr];
+      part += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+    }
+    norm_partial(0, a.j0, part);
+  }
+
+  for (int kk = 0; kk < kb; ++kk) {
+    const int J = a.j0 + kk, par = kk & 1;
+    T* x = P + kk * rb;
+    cluster_sync();
+    // reflector, identical in every CTA (partials combined in the same order)
+    if (warp == 0) {
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+      if (lane < (int)cs) {
+        v0 = ld_dsmem_f64(map_cta(&s_r1[par][0], lane));
+        v1 = ld_dsmem_f64(map_cta(&s_r1[par][1], lane));
+        v2 = ld_dsmem_f64(map_cta(&s_r1[par][2], lane));
+      }
+      for (int o = 1; o < kClusterMax; o <<= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+      }
+      if (lane == 0) {
+        const double xn = v0;
+        const c128 al = mk<double>(v1, v2);
+        c128 tau, sc, beta;
+        if (xn == 0.0 && al.im == 0.0) {
+          tau = mk<double>(0, 0);
+          sc = mk<double>(0, 0);
+          beta = al;
+        } else {
+          const double nv = sqrt(al.re * al.re + al.im * al.im + xn);
+          const double bt = al.re >= 0.0 ? -nv : nv;
+          tau = mk<double>((bt - al.re) / bt, -al.im / bt);
+          const c128 dnm = mk<double>(al.re - bt, al.im);
+          const double dd = dnm.re * dnm.re + dnm.im * dnm.im;
+          sc = mk<double>(dnm.re / dd, -dnm.im / dd);  // 1 / (alpha - beta)
+          beta = mk<double>(bt, 0.0);
+        }
+        s_sc[0] = tau;
+        s_sc[1] = sc;
+        s_sc[2] = beta;
+      }
+    }
+    __syncthreads();
+    const T tau = ccast<R>(s_sc[0]), sc = ccast<R>(s_sc[1]);
+    const int rs = max(0, J - r0);  // first local row >= J
+    // partial d_c = sum_{r >= J} conj(v_r) W[r, c] with v_J = 1, v_r = x_r / (alpha - beta)
+    for (int c0 = warp; c0 < kb; c0 += 2 * CPW) {
+      const int c1 = c0 + CPW;
+      const T* col0 = P + c0 * rb;
+      const T* col1 = P + min(c1, kb - 1) * rb;
+      T acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+      for (int rr = rs + lane; rr < nr; rr += 32) {
+        const T v = cconj((r0 + rr == J) ? mk<R>(1, 0) : x[rr] * sc);
+        cfma(acc0, v, col0[rr]);
+        cfma(acc1, v, col1[rr]);
+      }
+      acc0.re = warp_sum(acc0.re);
+      acc0.im = warp_sum(acc0.im);
+      acc1.re = warp_sum(acc1.re);
+      acc1.im = warp_sum(acc1.im);
+      if (lane == 0) {
+        s_r2[par][c0] = acc0;
+        if (c1 < kb) s_r2[par][c1] = acc1;
+      }
+    }
+    cluster_sync();
+    // d_c summed over the cluster (16 lanes per column)
+    {
+      const int c = tid / kClusterMax, q = tid % kClusterMax;
+      T v = mk<R>(0, 0);
+      if (c < kb && q < (int)cs) v = ld_dsmem(static_cast<const T*>(nullptr), map_cta(&s_r2[par][c], q));
+      for (int o = 1; o < kClusterMax; o <<= 1) {
+        v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+        v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+      }
+      if (c < kb && q == 0) {
+        s_d[c] = v;
+        s_f[c] = cconj(tau) * v;
+      }
+    }
+    __syncthreads();
+    if (rank == 0) {
+      if (tid < kk) a.Wg[(int64_t)kk * a.nb + tid] = ccast<double>(cconj(s_d[tid]));
+      if (tid == 32) a.tau[J] = tau;
+    }
+    // v stored in place of x; trailing panel columns W[J:m, c] -= v conj(tau) d_c;
+    // the next column's norm below row J+1 is accumulated on the way
+    double part = 0.0;
+    for (int rr = rs + tid; rr < nr; rr += CPT) {
+      const int r = r0 + rr;
+      T v = mk<R>(1, 0);
+      if (r > J) {
+        v = x[rr] * sc;
+        x[rr] = v;
+      }
+      for (int c = kk + 1; c < kb; ++c) {
+        T* col = P + c * rb;
+        const T nv = col[rr] - v * s_f[c];
+        col[rr] = nv;
+        if (c == kk + 1 && r > J + 1) part += (double)nv.re * (double)nv.re + (double)nv.im * (double)nv.im;
+      }
+    }
+    if (J >= r0 && J < r1 && tid == 0) x[J - r0] = ccast<R>(s_sc[2]);  // R diagonal
+    if (kk + 1 < kb) norm_partial(kk + 1, J + 1, part);  // contains __syncthreads
+    __syncthreads();
+  }
+  cluster_sync();  // no CTA leaves while another may still read its shared memory
+  for (int c = 0; c < kb; ++c)
+    for (int rr = tid; rr < nr; rr += CPT) a.W[(r0 + rr) + (int64_t)(a.j0 + c) * a.ldw] = P[c * rb + rr];
+}
+
 // Triangular factor of each panel's block reflector (H_j0 ... H_j0+kb-1 =
 // I - V T V^H, forward columnwise), built by recursive doubling: the factor
 // of [V1 V2] is [[T1, -T1 (V1^H V2) T2], [0, T2]], so starting from the
@@ -962,6 +1180,45 @@ int num_sms() {
 }
 
 constexpr int kPanelSmem = 200 * 1024;  // dynamic shared memory of the panel kernel
+
+constexpr int kCPanelSmem = 200 * 1024;
+
+// Cluster size usable for the unpivoted panel kernel on this device (16 when
+// non-portable clusters of 16 CTAs with the full shared-memory carve-out can
+// be resident, else 8, else 0 = not available).
+template <typename T>
+static int cpanel_cluster_size() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  cached = 0;
+  if (cudaFuncSetAttribute(qr_cpanel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCPanelSmem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return cached;
+  }
+  cudaFuncSetAttribute(qr_cpanel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaGetLastError();
+  for (int cs : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(CPT);
+    cfg.dynamicSmemBytes = kCPanelSmem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, qr_cpanel_kernel<T>, &cfg) == cudaSuccess && n >= 1) {
+      cached = cs;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return cached;
+}
 
 template <typename T>
 static cudaError_t panel_setup(int& max_blocks) {
@@ -1207,7 +1464,36 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     }
     void* args[] = {&a};
     hook_before(hooks, K(MPS_KCLASS_PANEL), bytes, flops);
-    CK(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<T>, dim3(G), dim3(PNT), args, (size_t)dyn, s));
+    // unpivoted panels whose rows fit the shared memory of one cluster run on it
+    const int ccs = p.pivot ? 0 : cpanel_cluster_size<T>();
+    const int crb = ccs > 0 ? ((m - j0 + ccs - 1) / ccs + 1) / 2 * 2 : 0;
+    if (ccs > 0 && (int64_t)kb * crb * (int64_t)sizeof(T) <= kCPanelSmem) {
+      CPanelArgs<T> ca;
+      ca.W = p.W;
+      ca.ldw = p.ldw;
+      ca.m = m;
+      ca.j0 = j0;
+      ca.kb = kb;
+      ca.nb = nb;
+      ca.rb = crb;
+      ca.tau = p.tau;
+      ca.Wg = a.Wg;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = ccs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(ccs);
+      cfg.blockDim = dim3(CPT);
+      cfg.dynamicSmemBytes = (size_t)kb * crb * sizeof(T);
+      cfg.stream = s;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      CK(cudaLaunchKernelEx(&cfg, qr_cpanel_kernel<T>, ca));
+    } else {
+      CK(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<T>, dim3(G), dim3(PNT), args, (size_t)dyn, s));
+    }
     hook_after(hooks, K(MPS_KCLASS_PANEL), 1);
     if (p.pivot) {
       if (J1 < n && J1 < m) {
