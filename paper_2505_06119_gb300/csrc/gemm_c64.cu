@@ -72,7 +72,10 @@ __device__ __forceinline__ int mask_kind(int mask, int r, int c) {
 
 // BM = 64 tiles run two CTAs per SM (at most 128 registers a thread) so one
 // CTA's C traffic overlaps the other's arithmetic in short contractions.
-template <int BM, bool THETA>
+// BETA: C is read (beta != 0, no split-K); compiled separately so the long
+// contractions, which never read C, keep the register allocation of a kernel
+// without that code.
+template <int BM, bool THETA, bool BETA>
 __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDesc<c64> d, ThetaEpi te) {
   constexpr int RG = BM / 32;             // row pairs per thread
   constexpr int EA = BM * G_BK / G_NT;    // A elements copied per thread and slice
@@ -91,8 +94,9 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
     kbeg = blockIdx.z * per;
     kend = min(d.K, kbeg + per);
   }
-  const bool beta_nz = !THETA && !split && !(d.beta.re == 0.f && d.beta.im == 0.f);
+  constexpr bool beta_nz = BETA && !THETA;  // the host launches BETA only without split-K
   const bool scale_a = !THETA && !split && !(d.alpha.re == 1.f && d.alpha.im == 0.f);
+  const bool alpha_neg = scale_a && d.alpha.re == -1.f && d.alpha.im == 0.f;
   const bool fix_a = scale_a || d.a_conj || d.a_mask == MASK_UNIT_LOWER;
   const bool fix_b = d.b_conj || d.b_mask == MASK_UNIT_LOWER;
 
@@ -161,7 +165,8 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
         c64* p = as + kk * LAS + ii;
         c64 v = kind == 2 ? mk<float>(1.f, 0.f) : *p;
         if (d.a_conj) v = cconj(v);
-        if (scale_a) v = d.alpha * v;
+        if (alpha_neg) v = mk<float>(-v.re, -v.im);
+        else if (scale_a) v = d.alpha * v;
         *p = v;
       }
     }
@@ -189,23 +194,40 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
   }
 
   float acc[2 * RG][8][2];
-  if (beta_nz) {
+  // C pairs (rows i, i+1) move as one 16-byte vector when C allows it
+  const bool cvec = ((reinterpret_cast<uintptr_t>(d.C) & 15) == 0) && ((d.ldc & 1) == 0);
+  const bool beta_one = d.beta.re == 1.f && d.beta.im == 0.f;
+  if constexpr (beta_nz) {
 #pragma unroll
-    for (int g = 0; g < RG; ++g)
+    for (int g = 0; g < RG; ++g) {
+      const int i = i0 + 32 * g + 2 * tm;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int i = i0 + 32 * g + 2 * tm + e;
+      for (int h = 0; h < 4; ++h)
 #pragma unroll
-        for (int h = 0; h < 4; ++h)
-#pragma unroll
-          for (int f = 0; f < 2; ++f) {
-            const int j = j0 + 32 * h + 2 * tn + f;
-            c64 v = mk<float>(0.f, 0.f);
-            if (i < d.M && j < d.N) v = d.beta * d.C[i + (int64_t)j * d.ldc];
-            acc[2 * g + e][2 * h + f][0] = v.re;
-            acc[2 * g + e][2 * h + f][1] = v.im;
+        for (int f = 0; f < 2; ++f) {
+          const int j = j0 + 32 * h + 2 * tn + f;
+          c64 v0 = mk<float>(0.f, 0.f), v1 = v0;
+          if (j < d.N) {
+            const c64* cp = d.C + i + (int64_t)j * d.ldc;
+            if (cvec && i + 1 < d.M) {
+              const float4 q = *reinterpret_cast<const float4*>(cp);
+              v0 = mk<float>(q.x, q.y);
+              v1 = mk<float>(q.z, q.w);
+            } else {
+              if (i < d.M) v0 = cp[0];
+              if (i + 1 < d.M) v1 = cp[1];
+            }
           }
-      }
+          if (!beta_one) {
+            v0 = d.beta * v0;
+            v1 = d.beta * v1;
+          }
+          acc[2 * g][2 * h + f][0] = v0.re;
+          acc[2 * g][2 * h + f][1] = v0.im;
+          acc[2 * g + 1][2 * h + f][0] = v1.re;
+          acc[2 * g + 1][2 * h + f][1] = v1.im;
+        }
+    }
   } else {
 #pragma unroll
     for (int a = 0; a < 2 * RG; ++a)
@@ -285,38 +307,46 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
       }
     }
   } else {
+    // destination: C, or this split's slice of the workspace (leading dimension M)
+    c64* dst = split ? d.wk + (int64_t)blockIdx.z * d.M * d.N : d.C;
+    const int64_t ldd = split ? d.M : d.ldc;
+    // 16-byte stores where allowed (the 128-row kernel without C reads keeps
+    // scalar stores: measured faster there)
+    const bool dvec = (BETA || BM == 64) && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && ((ldd & 1) == 0);
 #pragma unroll
-    for (int g = 0; g < RG; ++g)
+    for (int g = 0; g < RG; ++g) {
+      const int i = i0 + 32 * g + 2 * tm;
+      if (i >= d.M) continue;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int i = i0 + 32 * g + 2 * tm + e;
-        if (i >= d.M) continue;
+      for (int h = 0; h < 4; ++h)
 #pragma unroll
-        for (int h = 0; h < 4; ++h)
-#pragma unroll
-          for (int f = 0; f < 2; ++f) {
-            const int j = j0 + 32 * h + 2 * tn + f;
-            if (j >= d.N) continue;
-            const c64 v = mk<float>(acc[2 * g + e][2 * h + f][0], acc[2 * g + e][2 * h + f][1]);
-            if (split)
-              d.wk[(int64_t)blockIdx.z * d.M * d.N + i + (int64_t)j * d.M] = v;
-            else
-              d.C[i + (int64_t)j * d.ldc] = v;
+        for (int f = 0; f < 2; ++f) {
+          const int j = j0 + 32 * h + 2 * tn + f;
+          if (j >= d.N) continue;
+          c64* cp = dst + i + (int64_t)j * ldd;
+          const float* a0 = acc[2 * g][2 * h + f];
+          const float* a1 = acc[2 * g + 1][2 * h + f];
+          if (dvec && i + 1 < d.M) {
+            *reinterpret_cast<float4*>(cp) = make_float4(a0[0], a0[1], a1[0], a1[1]);
+          } else {
+            cp[0] = mk<float>(a0[0], a0[1]);
+            if (i + 1 < d.M) cp[1] = mk<float>(a1[0], a1[1]);
           }
-      }
+        }
+    }
   }
 }
 
-template <int BM, bool THETA>
+template <int BM, bool THETA, bool BETA>
 cudaError_t launch(const GemmDesc<c64>& d, const ThetaEpi& te, dim3 grid, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_c64_kernel<BM, THETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         g_smem_bytes<BM>());
+    cudaError_t e = cudaFuncSetAttribute(gemm_c64_kernel<BM, THETA, BETA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem_bytes<BM>());
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  gemm_c64_kernel<BM, THETA><<<grid, G_NT, g_smem_bytes<BM>(), s>>>(d, te);
+  gemm_c64_kernel<BM, THETA, BETA><<<grid, G_NT, g_smem_bytes<BM>(), s>>>(d, te);
   return cudaGetLastError();
 }
 
@@ -331,7 +361,9 @@ cudaError_t gemm_c64(const GemmDesc<c64>& d, cudaStream_t s) {
   const int BM = gemm_c64_tile_rows(d.M, d.K);
   dim3 grid((d.M + BM - 1) / BM, (d.N + G_BN - 1) / G_BN, d.splitk > 1 ? d.splitk : 1);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-  return BM == 128 ? launch<128, false>(d, te, grid, s) : launch<64, false>(d, te, grid, s);
+  const bool beta = d.splitk <= 1 && !(d.beta.re == 0.f && d.beta.im == 0.f);
+  if (BM == 128) return beta ? launch<128, false, true>(d, te, grid, s) : launch<128, false, false>(d, te, grid, s);
+  return beta ? launch<64, false, true>(d, te, grid, s) : launch<64, false, false>(d, te, grid, s);
 }
 
 cudaError_t theta_c64(int cl, int cm, int cr, const c64* A, const c64* B, const c64* g16, c64* W, int64_t ldw,
@@ -355,7 +387,7 @@ cudaError_t theta_c64(int cl, int cm, int cr, const c64* A, const c64* B, const 
   te.ldw = ldw;
   dim3 grid((d.M + 127) / 128, (cr + G_BN / 2 - 1) / (G_BN / 2), 1);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  return launch<128, true>(d, te, grid, s);
+  return launch<128, true, false>(d, te, grid, s);
 }
 
 }  // namespace mpsg

@@ -50,6 +50,8 @@ constexpr int kDChMax = 32;      // row chunks per column in phase D (about 8 KB
 constexpr int kDpCap = kDBatch * kDChMax;  // phase-D chunk sums held at once
 constexpr int kSlot = 4096;      // bytes of one bulk-copy slot (phase D, bulk mode)
 constexpr int kRing = PNW * 2 * kSlot;  // two slots per warp
+constexpr int kNSW = 2;                 // warps on the reflector scalars in bulk mode
+constexpr int kNDW = PNW - kNSW;        // warps on the trailing sweep in bulk mode
 
 template <typename T>
 struct PanelArgs {
@@ -309,7 +311,8 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw + a.xs_off);
   __shared__ __align__(8) unsigned long long s_mbar[PNW][2];  // bulk mode: one barrier per slot
-  __shared__ T s_w[kPanelNbMax];      // w_i = V_i^H v
+  __shared__ T s_wacc[kPanelNbMax];   // sum over CTAs of V_i^H x below row J
+  __shared__ __align__(8) unsigned long long s_xbar;  // bulk mode: x staging copy
   __shared__ T s_vrow[kPanelNbMax];   // W[J, j0+i]
   __shared__ T s_wp[PNW][kPanelNbMax];  // per-warp partials of V^H x (phase B)
   __shared__ T s_dp[kDpCap];  // phase-D chunk sums
@@ -328,8 +331,10 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   if (a.bulk && lane == 0) {
     mbar_init(smem_u32(&s_mbar[warp][0]), 1);
     mbar_init(smem_u32(&s_mbar[warp][1]), 1);
+    if (warp == 0) mbar_init(smem_u32(&s_xbar), 1);
   }
-  unsigned ph = 0;  // bulk mode: parity of the next completion of this warp's slots
+  unsigned ph = 0;   // bulk mode: parity of the next completion of this warp's slots
+  unsigned xph = 0;  // bulk mode: parity of the next completion of the x copy
   __syncthreads();
   if (s_skip) return;
 
@@ -501,38 +506,33 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     if (a.bulk) fence_proxy_async();  // phase-B writes (column swap) before later bulk reads
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
 
-    // ---------------- C: reflector (every CTA, identical FP64 arithmetic)
+    // ---------------- C: reflector (every CTA, identical FP64 arithmetic).
+    // Warp 0 computes beta, tau and 1/(alpha - beta) in FP64; warp 1 combines the
+    // CTAs' partial sums of V^H x.  In bulk mode x is staged by one bulk copy and
+    // the other warps go straight on to the trailing sweep (phase D1), which needs
+    // only x; the reflector scalars are first used in the D2 epilogue.
     const int L = m - J - 1;  // rows below the pivot row
     // x = W[J+1:m, J] staged from the even row xbase (16-byte aligned vectors)
     const int xbase = (sizeof(T) == 8) ? ((J + 1) & ~1) : (J + 1);
     const bool staged = (m - xbase <= a.xcap);
-    // all loads of this phase first: partial sums, row J of V, x for phase D
-    double nv[5];
-    c128 al = mk<double>(0, 0);
+    const bool xcopy = a.bulk && staged && m > xbase;  // x arrives by bulk copy this step
+    if (xcopy && tid == 0) {
+      const uint32_t bytes = (uint32_t)((m - xbase) * sizeof(T));
+      fence_proxy_async();  // phase-B writes of column J, and last step's reads of xs
+      mbar_expect_tx(smem_u32(&s_xbar), bytes);
+      bulk_g2s(smem_u32(xs), colJ + xbase, bytes, smem_u32(&s_xbar));
+    }
+    if (!a.bulk && staged)
+      for (int r = tid; r < m - xbase; r += PNT) xs[r] = colJ[xbase + r];
     if (warp == 0) {
+      double nv[5];
+      c128 al = mk<double>(0, 0);
 #pragma unroll
       for (int u = 0; u < 5; ++u) {
         const int g = lane + 32 * u;
         nv[u] = g < gb ? a.red_norm[g] : 0.0;
       }
       if (lane == 0) al = *a.alpha_slot;
-    }
-    T wv[2][5];
-    T vrw[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = warp + PNW * q;
-      vrw[q] = mk<R>(0, 0);
-#pragma unroll
-      for (int u = 0; u < 5; ++u) {
-        const int g = lane + 32 * u;
-        wv[q][u] = (i < kk && g < gb) ? a.red_w[(int64_t)g * nb + i] : mk<R>(0, 0);
-      }
-      if (i < kk && lane == 0) vrw[q] = W[J + (int64_t)(a.j0 + i) * ldw];
-    }
-    if (staged)
-      for (int r = tid; r < m - xbase; r += PNT) xs[r] = colJ[xbase + r];
-    if (warp == 0) {
       double xn = 0.0;
 #pragma unroll
       for (int u = 0; u < 5; ++u) xn += nv[u];
@@ -557,34 +557,23 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         s_scal[1] = sc;
         s_scal[2] = beta;
       }
-    }
-    __syncthreads();
-    // tau and 1/(alpha-beta) are FP64 results; the data path uses them rounded
-    const T tau = ccast<R>(s_scal[0]), sc = ccast<R>(s_scal[1]);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = warp + PNW * q;
+    } else if (warp == 1 && lane < kk) {
+      // lane i: sum over the CTAs of V_i^H x (below row J), in CTA order; row J of V
       T acc = mk<R>(0, 0);
-#pragma unroll
-      for (int u = 0; u < 5; ++u) acc = acc + wv[q][u];
-      if (i < kk)
-        for (int g = lane + 160; g < gb; g += 32) acc = acc + a.red_w[(int64_t)g * nb + i];
-      acc.re = warp_sum(acc.re);
-      acc.im = warp_sum(acc.im);
-      if (i < kk && lane == 0) {
-        s_vrow[i] = vrw[q];
-        s_w[i] = cconj(vrw[q]) + sc * acc;  // V_i^H v
+      int g = 0;
+      for (; g + 4 <= gb; g += 4) {
+        const T p0 = a.red_w[(int64_t)g * nb + lane], p1 = a.red_w[(int64_t)(g + 1) * nb + lane];
+        const T p2 = a.red_w[(int64_t)(g + 2) * nb + lane], p3 = a.red_w[(int64_t)(g + 3) * nb + lane];
+        acc = acc + p0;
+        acc = acc + p1;
+        acc = acc + p2;
+        acc = acc + p3;
       }
+      for (; g < gb; ++g) acc = acc + a.red_w[(int64_t)g * nb + lane];
+      s_wacc[lane] = acc;
+      s_vrow[lane] = W[J + (int64_t)(a.j0 + lane) * ldw];
     }
-    __syncthreads();
-    if (b == 0) {
-      // w of this step, for the triangular factor T of the panel (tfactor_kernel)
-      if (tid < kk) a.Wg[(int64_t)kk * nb + tid] = ccast<double>(s_w[tid]);
-      if (tid == 32) {
-        a.tau[J] = tau;
-        W[J + (int64_t)J * ldw] = ccast<R>(s_scal[2]);
-      }
-    }
+    if (!a.bulk) __syncthreads();
 
     // ---------------- D: trailing columns in batches of up to kDBatch; each column's
     // sweep y_t = W[J+1:m, t]^H x is cut into row chunks of about 8 KB so that
@@ -606,16 +595,24 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     const int nchb = a.bulk ? (Lx + CR - 1) / CR : nch;  // chunks per column
     const int nbc = a.bulk ? max(1, min(kDBatch, kDpCap / max(nchb, 1))) : kDBatch;
     if (a.bulk && lane == 0) fence_proxy_async();  // generic writes before the barrier -> async reads
+    bool xseen = false;
     for (int cb = c0; cb < c1; cb += nbc) {
       const int nc = min(nbc, c1 - cb);
       // D1: chunk sums
       if (a.bulk) {
+        // items (column, chunk) dealt round-robin to the sweep warps kNSW..PNW-1
+        const int dw = warp - kNSW;
         const int nit = nc * nchb;
-        const int nli = nit > warp ? (nit - warp + PNW - 1) / PNW : 0;  // this warp's items
+        const int nli = (dw >= 0 && nit > dw) ? (nit - dw + kNDW - 1) / kNDW : 0;  // this warp's items
         unsigned char* slot0 = smem_raw + warp * 2 * kSlot;
+        if (nli > 0 && xcopy && !xseen) {  // x staged by the bulk copy of phase C
+          if (!mbar_wait(smem_u32(&s_xbar), xph, a.err, a.timeout_ns))
+            mbar_wait_plain(smem_u32(&s_xbar), xph, a.timeout_ns);
+          xseen = true;
+        }
         if (lane == 0) {
           for (int li = 0; li < min(2, nli); ++li) {
-            const int it = warp + PNW * li, cl = it / nchb, ch = it - cl * nchb;
+            const int it = dw + kNDW * li, cl = it / nchb, ch = it - cl * nchb;
             const int cs = xbase + ch * CR, ce = min(m, cs + CR);
             const uint32_t mb = smem_u32(&s_mbar[warp][li]);
             mbar_expect_tx(mb, (uint32_t)((ce - cs) * sizeof(T)));
@@ -625,7 +622,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         }
         for (int li = 0; li < nli; ++li) {
           const int q = li & 1;
-          const int it = warp + PNW * li, cl = it / nchb, ch = it - cl * nchb;
+          const int it = dw + kNDW * li, cl = it / nchb, ch = it - cl * nchb;
           const int cs = xbase + ch * CR, ce = min(m, cs + CR);
           const uint32_t mb = smem_u32(&s_mbar[warp][q]);
           const uint32_t par = (ph >> q) & 1u;
@@ -637,7 +634,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           if (lane == 0) s_dp[cl * nchb + ch] = s;
           __syncwarp();
           if (lane == 0 && li + 2 < nli) {
-            const int it2 = it + 2 * PNW, cl2 = it2 / nchb, ch2 = it2 - cl2 * nchb;
+            const int it2 = it + 2 * kNDW, cl2 = it2 / nchb, ch2 = it2 - cl2 * nchb;
             const int cs2 = xbase + ch2 * CR, ce2 = min(m, cs2 + CR);
             fence_proxy_async();  // this slot's reads before the next asynchronous write into it
             mbar_expect_tx(mb, (uint32_t)((ce2 - cs2) * sizeof(T)));
@@ -657,7 +654,10 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         }
       }
       __syncthreads();
-      // D2: per-column epilogue; operands of all of this warp's columns fetched first
+      // D2: per-column epilogue; operands of all of this warp's columns fetched first.
+      // tau and 1/(alpha-beta) are FP64 results; the data path uses them rounded.
+      const T tau = ccast<R>(s_scal[0]), sc = ccast<R>(s_scal[1]);
+      const T w_l = lane < kk ? cconj(s_vrow[lane]) + sc * s_wacc[lane] : mk<R>(0, 0);  // V_l^H v
       constexpr int CPW = kDBatch / PNW;  // columns per warp
       T wJtT[CPW], fiT[CPW];
       double v1a[CPW], v2a[CPW];
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         T fw = mk<R>(0, 0), rowu = mk<R>(0, 0);
         if (lane < kk) {
           const T fi = fiT[q];
-          cfma(fw, fi, s_w[lane]);
+          cfma(fw, fi, w_l);
           cfma(rowu, s_vrow[lane], cconj(fi));
           if (t == p) Ft[lane] = fi;
         }
@@ -764,6 +764,22 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         a.red_argv[b] = bv;
         a.red_argi[b] = bi;
       }
+    }
+    __syncthreads();  // reflector scalars complete even where this CTA had no trailing columns
+    if (b == 0) {
+      // w of this step, for the triangular factor T of the panel (tfactor_kernel)
+      const T scd = ccast<R>(s_scal[1]);
+      if (tid < kk) a.Wg[(int64_t)kk * nb + tid] = ccast<double>(cconj(s_vrow[tid]) + scd * s_wacc[tid]);
+      if (tid == 32) {
+        a.tau[J] = ccast<R>(s_scal[0]);
+        W[J + (int64_t)J * ldw] = ccast<R>(s_scal[2]);
+      }
+    }
+    if (xcopy) {
+      // the x copy has landed before xs is staged again or the CTA leaves
+      if (tid == 0 && !mbar_wait(smem_u32(&s_xbar), xph, a.err, a.timeout_ns))
+        mbar_wait_plain(smem_u32(&s_xbar), xph, a.timeout_ns);
+      xph ^= 1u;
     }
     s_prev = s_scal[1];
     if (a.bulk) fence_proxy_async();  // this step's generic writes before later bulk reads
