@@ -13,14 +13,15 @@
 // copies of slice s + kStages - 1 are in flight while slice s is multiplied,
 // and no register holds staged data.  Elements outside the matrix or zero
 // under the operand mask are zero-filled by the copy; what a plain copy cannot
-// express (conjugation, the unit diagonal of a reflector block, the scalar
-// alpha) is applied by each thread to the elements it copied, after they land
-// and before the slice is published to the CTA.
+// express (conjugation, the unit diagonal of a reflector block) is applied by
+// each thread to the elements it copied, after they land and before the slice
+// is published to the CTA.
 //
-// With beta != 0 the accumulators start from beta * C (those loads overlap the
-// first operand copies) and alpha is folded into the A slices, so the epilogue
-// is a plain store: C = beta C + sum_k (alpha A)(i,k) B(k,j).  With split-K the
-// raw partial products go to the workspace and a reduction applies alpha/beta.
+// The product sum is accumulated from zero and rounded on its own before the
+// epilogue forms C = alpha * sum + beta * C (C read only by the C-reading
+// variant of the kernel), which keeps a small update from being rounded at the
+// scale of C once per K step.  With split-K the raw partial products go to the
+// workspace and a reduction applies alpha and beta.
 //
 // Theta mode: A is the row-major site A_i ((l,c) x mu), B the row-major site
 // A_{i+1} (mu x (d,r)); the tile's 128 columns are 64 values of r for both d,
@@ -95,9 +96,7 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
     kend = min(d.K, kbeg + per);
   }
   constexpr bool beta_nz = BETA && !THETA;  // the host launches BETA only without split-K
-  const bool scale_a = !THETA && !split && !(d.alpha.re == 1.f && d.alpha.im == 0.f);
-  const bool alpha_neg = scale_a && d.alpha.re == -1.f && d.alpha.im == 0.f;
-  const bool fix_a = scale_a || d.a_conj || d.a_mask == MASK_UNIT_LOWER;
+  const bool fix_a = d.a_conj || d.a_mask == MASK_UNIT_LOWER;
   const bool fix_b = d.b_conj || d.b_mask == MASK_UNIT_LOWER;
 
   // this thread's copy slots: element e of A sits at tile (ia + e*dia, ka + e*dka),
@@ -165,8 +164,6 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
         c64* p = as + kk * LAS + ii;
         c64 v = kind == 2 ? mk<float>(1.f, 0.f) : *p;
         if (d.a_conj) v = cconj(v);
-        if (alpha_neg) v = mk<float>(-v.re, -v.im);
-        else if (scale_a) v = d.alpha * v;
         *p = v;
       }
     }
@@ -194,41 +191,7 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
   }
 
   float acc[2 * RG][8][2];
-  // C pairs (rows i, i+1) move as one 16-byte vector when C allows it
-  const bool cvec = ((reinterpret_cast<uintptr_t>(d.C) & 15) == 0) && ((d.ldc & 1) == 0);
-  const bool beta_one = d.beta.re == 1.f && d.beta.im == 0.f;
-  if constexpr (beta_nz) {
-#pragma unroll
-    for (int g = 0; g < RG; ++g) {
-      const int i = i0 + 32 * g + 2 * tm;
-#pragma unroll
-      for (int h = 0; h < 4; ++h)
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          const int j = j0 + 32 * h + 2 * tn + f;
-          c64 v0 = mk<float>(0.f, 0.f), v1 = v0;
-          if (j < d.N) {
-            const c64* cp = d.C + i + (int64_t)j * d.ldc;
-            if (cvec && i + 1 < d.M) {
-              const float4 q = *reinterpret_cast<const float4*>(cp);
-              v0 = mk<float>(q.x, q.y);
-              v1 = mk<float>(q.z, q.w);
-            } else {
-              if (i < d.M) v0 = cp[0];
-              if (i + 1 < d.M) v1 = cp[1];
-            }
-          }
-          if (!beta_one) {
-            v0 = d.beta * v0;
-            v1 = d.beta * v1;
-          }
-          acc[2 * g][2 * h + f][0] = v0.re;
-          acc[2 * g][2 * h + f][1] = v0.im;
-          acc[2 * g + 1][2 * h + f][0] = v1.re;
-          acc[2 * g + 1][2 * h + f][1] = v1.im;
-        }
-    }
-  } else {
+  {
 #pragma unroll
     for (int a = 0; a < 2 * RG; ++a)
 #pragma unroll
@@ -310,9 +273,10 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
     // destination: C, or this split's slice of the workspace (leading dimension M)
     c64* dst = split ? d.wk + (int64_t)blockIdx.z * d.M * d.N : d.C;
     const int64_t ldd = split ? d.M : d.ldc;
-    // 16-byte stores where allowed (the 128-row kernel without C reads keeps
+    // 16-byte accesses where allowed (the 128-row kernel without C reads keeps
     // scalar stores: measured faster there)
     const bool dvec = (BETA || BM == 64) && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && ((ldd & 1) == 0);
+    const bool alpha_one = split || (d.alpha.re == 1.f && d.alpha.im == 0.f);
 #pragma unroll
     for (int g = 0; g < RG; ++g) {
       const int i = i0 + 32 * g + 2 * tm;
@@ -324,13 +288,31 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
           const int j = j0 + 32 * h + 2 * tn + f;
           if (j >= d.N) continue;
           c64* cp = dst + i + (int64_t)j * ldd;
-          const float* a0 = acc[2 * g][2 * h + f];
-          const float* a1 = acc[2 * g + 1][2 * h + f];
-          if (dvec && i + 1 < d.M) {
-            *reinterpret_cast<float4*>(cp) = make_float4(a0[0], a0[1], a1[0], a1[1]);
+          const bool pair = i + 1 < d.M;
+          c64 v0 = mk<float>(acc[2 * g][2 * h + f][0], acc[2 * g][2 * h + f][1]);
+          c64 v1 = mk<float>(acc[2 * g + 1][2 * h + f][0], acc[2 * g + 1][2 * h + f][1]);
+          if (!alpha_one) {
+            v0 = d.alpha * v0;
+            v1 = d.alpha * v1;
+          }
+          if constexpr (beta_nz) {  // C = alpha sum + beta C, the sum rounded on its own first
+            c64 c0, c1 = mk<float>(0.f, 0.f);
+            if (dvec && pair) {
+              const float4 q = *reinterpret_cast<const float4*>(cp);
+              c0 = mk<float>(q.x, q.y);
+              c1 = mk<float>(q.z, q.w);
+            } else {
+              c0 = cp[0];
+              if (pair) c1 = cp[1];
+            }
+            v0 = v0 + d.beta * c0;
+            v1 = v1 + d.beta * c1;
+          }
+          if (dvec && pair) {
+            *reinterpret_cast<float4*>(cp) = make_float4(v0.re, v0.im, v1.re, v1.im);
           } else {
-            cp[0] = mk<float>(a0[0], a0[1]);
-            if (i + 1 < d.M) cp[1] = mk<float>(a1[0], a1[1]);
+            cp[0] = v0;
+            if (pair) cp[1] = v1;
           }
         }
     }
