@@ -429,6 +429,52 @@ def reference(args):
     print(json.dumps(line), flush=True)
 
 
+def layer_workload(args):
+    """Layer batching (a 64-qubit chain, bonds 2..chi, random canonical state, mixed
+    precision, LOCAL policy): one brick-wall layer of Haar SU(4) gates on the even and
+    on the odd bonds, applied by mps_apply_layer and one gate at a time; per-layer
+    milliseconds of each (CUDA-synchronised wall clock, after one warm-up layer)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from workloads import gates, states
+
+    __graft_entry__.build()
+    from paper_2505_06119_gb300 import MPS
+
+    n = 64
+    out = {"workload": "layer", "n_sites": n, "precision": "mixed", "policy": "local", "rows": []}
+    for chi in [int(c) for c in args.layer_chi.split(",")]:
+        sites = [s.astype(np.complex64) for s in states.random_canonical_mps(n, states.max_bond_dims(n, chi), n // 2,
+                                                                            seed=5)]
+        rng = np.random.default_rng(3)
+        row = {"chi": chi}
+        for par in (0, 1):
+            bonds = list(range(par, n - 1, 2))
+            gs = [gates.haar_unitary(rng, 4) for _ in bonds]
+            res = {}
+            for mode in ("layer", "one_by_one"):
+                with MPS(n, chi, precision="mixed", policy="local") as m:
+                    for rep in range(2):  # warm-up layer, then the timed one
+                        m.set_sites(sites, centre=n // 2)
+                        m.sync()
+                        torch.cuda.synchronize()
+                        t = time.perf_counter()
+                        if mode == "layer":
+                            m.apply_layer(bonds, gs)
+                        else:
+                            for q, g in zip(bonds, gs):
+                                m.apply_2q(q, g)
+                        m.sync()
+                        res[mode] = (time.perf_counter() - t) * 1e3
+            row["even" if par == 0 else "odd"] = {"gates": len(bonds), "ms_layer": res["layer"],
+                                                  "ms_one_by_one": res["one_by_one"],
+                                                  "speedup": res["one_by_one"] / res["layer"]}
+        out["rows"].append(row)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,8 +488,13 @@ def main():
     ap.add_argument("--cpu-chi", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-overlap", action="store_true")
+    ap.add_argument("--workload", default="gate", choices=["gate", "layer"],
+                    help="gate: the headline metric; layer: batched vs one-by-one layer times")
+    ap.add_argument("--layer-chi", default="256,1024,2048")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "layer":
+        layer_workload(args)
+    elif args.impl == "reference":
         reference(args)
     else:
         ours(args)

@@ -46,7 +46,11 @@ struct WsLayout {
   int64_t sk_elems;
 };
 
-WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int64_t& ldw, int64_t& ldq) {
+// sk_wide > 0 sizes the split-K partials for that many columns instead of
+// max(nmax, kmax): workspaces that must choose the same splits as a larger one
+// (the layer lanes) get the larger one's partial capacity.
+WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int64_t& ldw, int64_t& ldq,
+                   int sk_wide = 0) {
   WsLayout L;
   ldw = (int64_t)std::max(4, (mmax + 3) / 4 * 4);
   ldq = ldw;
@@ -72,7 +76,7 @@ WsLayout ws_layout(size_t esz, int mmax, int nmax, int kmax, int nb, int G, int6
   L.G12 = take(esz * (size_t)nb * nb);
   L.Y = take(esz * (size_t)2 * nb * std::max(wide, 1));
   L.Z = take(esz * (size_t)2 * nb * std::max(wide, 1));
-  L.sk_elems = (int64_t)kMaxSplit * 2 * nb * std::max(wide, 1);
+  L.sk_elems = (int64_t)kMaxSplit * 2 * nb * std::max(sk_wide > 0 ? sk_wide : wide, 1);
   L.SK = take(esz * (size_t)L.sk_elems);
   L.red_norm = take(8 * (size_t)G);
   L.red_w = take(16 * (size_t)G * nb);
@@ -310,6 +314,16 @@ struct Profiler {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// A lane of the layer path: its own stream and a workspace for gates up to
+// kLaneDim rows and columns, so that small gates of one layer run concurrently.
+struct Lane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  char* ws = nullptr;
+  WsLayout L;
+  int64_t ldw = 0, ldq = 0;
+};
+
 struct mps_s {
   int n = 0, chi_max = 0, prec = MPS_PREC_FP64, policy = MPS_POLICY_CANON, device = 0;
   cudaStream_t stream = nullptr, own_stream = nullptr;
@@ -336,6 +350,9 @@ struct mps_s {
   c128* d_E = nullptr;
   size_t E_elems = 0;
   long long nsplit = 0;
+  // layer path (lazy)
+  std::vector<Lane> lanes;
+  cudaEvent_t ev_fork = nullptr;
   // status
   int status = MPS_OK;
   std::string msg;
@@ -379,6 +396,16 @@ void* dev_alloc(mps_t h, size_t bytes) {
 void release(mps_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (Lane& ln : h->lanes) {
+    if (ln.stream) {
+      cudaStreamSynchronize(ln.stream);
+      cudaStreamDestroy(ln.stream);
+    }
+    if (ln.done) cudaEventDestroy(ln.done);
+  }
+  h->lanes.clear();
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  h->ev_fork = nullptr;
   h->prof.destroy();
   for (void* p : h->allocs) {
     if (h->ufree)
@@ -552,6 +579,126 @@ int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
   h->bond[i + 1] = k;
   h->nsplit++;
   if (h->policy == MPS_POLICY_CANON) h->centre = i + 1;
+  return MPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Layer path (batching of a circuit layer's gates on disjoint bonds): gates
+// whose theta is at most kLaneDim x kLaneDim run concurrently on kLanes lanes
+// (own stream and workspace each, greedy balance by work), larger ones in order
+// on the handle's stream, which then waits for every lane.  Gates touch
+// disjoint sites, so the order between them does not matter; the discarded
+// weights are logged per gate and added to the total in gate order afterwards,
+// so the total is the same sum as on the one-by-one path.
+constexpr int kLanes = 8;
+constexpr int kLaneDim = 4096;
+
+__global__ void add_slots_kernel(const double* log, int first, int count, double* total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = *total;
+    for (int j = 0; j < count; ++j) t += log[(first + j) % kDiscLog];
+    *total = t;
+  }
+}
+
+int lanes_ready(mps_t h) {
+  if (!h->lanes.empty()) return MPS_OK;
+  const int dim = std::min(kLaneDim, 2 * h->chicap);
+  CUTRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "layer lanes");
+  h->lanes.resize(kLanes);
+  for (Lane& ln : h->lanes) {
+    CUTRY(h, cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking), "layer lanes");
+    CUTRY(h, cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming), "layer lanes");
+    // same split-K capacity as the handle's workspace: a lane makes the same
+    // split choices, so a layer gives exactly the one-by-one result
+    ln.L = ws_layout(h->esz, dim, dim, dim, h->kn.nb, h->kn.G, ln.ldw, ln.ldq, 2 * h->chicap);
+    ln.ws = (char*)dev_alloc(h, ln.L.total);
+    if (!ln.ws) return fail(h, MPS_E_NOMEM, "layer lanes: workspace");
+    // the allocation is stream-ordered on the handle's stream; the lane starts after it
+    CUTRY(h, cudaMemsetAsync(ln.ws + ln.L.bar, 0, 16, h->stream), "layer lanes");
+  }
+  CUTRY(h, cudaStreamSynchronize(h->stream), "layer lanes");
+  return MPS_OK;
+}
+
+template <typename T>
+int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi) {
+  if (h->prof.enabled || count <= 1) {  // per-class event timing needs one stream
+    for (int j = 0; j < count; ++j) {
+      int rc = apply_2q_t<T>(h, sites[j], gates + 16 * j, chi);
+      if (rc) return rc;
+    }
+    return MPS_OK;
+  }
+  int rc = lanes_ready(h);
+  if (rc) return rc;
+  struct Item {
+    int j, cl, cm, cr, k;
+    double work;
+  };
+  std::vector<Item> small, big;
+  for (int j = 0; j < count; ++j) {
+    const int i = sites[j];
+    Item it;
+    it.j = j;
+    it.cl = h->bond[i];
+    it.cm = h->bond[i + 1];
+    it.cr = h->bond[i + 2];
+    it.k = std::min(std::min(2 * it.cl, 2 * it.cr), chi);
+    const double m = 2.0 * it.cl, n = 2.0 * it.cr;
+    it.work = m * n * (it.cm + it.k) + 1e6;  // contraction + factorisation, plus a fixed latency share
+    (2 * it.cl <= kLaneDim && 2 * it.cr <= kLaneDim ? small : big).push_back(it);
+  }
+  std::sort(small.begin(), small.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
+  const int64_t first = h->nsplit;
+  auto slot_of = [&](int j) { return h->d_disclog + ((first + j) % kDiscLog); };
+  CUTRY(h, cudaEventRecord(h->ev_fork, h->stream), "layer fork");
+  std::vector<double> load(kLanes, 0.0);
+  std::vector<char> used(kLanes, 0);
+  const int* err_main = views<T>(h).err;
+  // lane gates share the SMs: each panel kernel gets a slice of them, but at
+  // least one CTA per 128 rows of theta, with which the per-CTA partial sums of
+  // every panel step are those of a full grid, so results do not change.
+  const int share = num_sms() / std::max(1, std::min<int>((int)small.size(), kLanes));
+  for (const Item& it : small) {
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    Lane& ln = h->lanes[l];
+    if (!used[l]) {
+      CUTRY(h, cudaStreamWaitEvent(ln.stream, h->ev_fork, 0), "layer fork");
+      used[l] = 1;
+    }
+    load[l] += it.work;
+    Ws<T> w = ws_views<T>(ln.ws, ln.L, ln.ldw, ln.ldq);
+    w.err = const_cast<int*>(err_main);  // one error word per handle
+    T gt[16];
+    gate_to_T<T>(gates + 16 * it.j, 16, gt);
+    const int i = sites[it.j];
+    Knobs kl = h->kn;
+    kl.G = std::min(h->kn.G, std::max((2 * it.cl + 127) / 128, share));
+    cudaError_t e = two_site_core<T>(w, kl, it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
+                                     (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1],
+                                     slot_of(it.j), nullptr, ln.stream, &h->prof.hooks);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer");
+  }
+  for (const Item& it : big) {
+    T gt[16];
+    gate_to_T<T>(gates + 16 * it.j, 16, gt);
+    const int i = sites[it.j];
+    cudaError_t e = two_site_core<T>(views<T>(h), h->kn, it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
+                                     (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1],
+                                     slot_of(it.j), nullptr, h->stream, &h->prof.hooks);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer");
+  }
+  for (int l = 0; l < kLanes; ++l) {
+    if (!used[l]) continue;
+    CUTRY(h, cudaEventRecord(h->lanes[l].done, h->lanes[l].stream), "layer join");
+    CUTRY(h, cudaStreamWaitEvent(h->stream, h->lanes[l].done, 0), "layer join");
+  }
+  add_slots_kernel<<<1, 32, 0, h->stream>>>(h->d_disclog, (int)(first % kDiscLog), count, h->d_scalar + 1);
+  CUTRY(h, cudaGetLastError(), "layer discarded");
+  for (const Item& it : small) h->bond[sites[it.j] + 1] = it.k;
+  for (const Item& it : big) h->bond[sites[it.j] + 1] = it.k;
+  h->nsplit += count;
   return MPS_OK;
 }
 
@@ -1068,11 +1215,10 @@ int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count,
     if (used[s] || used[s + 1]) return fail(h, MPS_E_ARG, "apply_layer: bonds overlap");
     used[s] = used[s + 1] = 1;
   }
-  for (int j = 0; j < count; ++j) {
-    rc = mps_apply_2q(h, sites[j], gates + 16 * j, chi_max);
-    if (rc) return rc;
-  }
-  return MPS_OK;
+  if (chi_max > h->chi_max) return fail(h, MPS_E_ARG, "apply_layer: chi_max above the handle's");
+  if (chi_max <= 0) chi_max = h->chi_max;
+  return h->prec == MPS_PREC_FP64 ? layer_t<c128>(h, sites, gates, count, chi_max)
+                                  : layer_t<c64>(h, sites, gates, count, chi_max);
 }
 
 int mps_amplitude(mps_t h, const uint8_t* bits, mps_c128* out) {

@@ -272,6 +272,28 @@ def test_apply_layer_equals_sequential():
             assert np.abs(a.get_site(i) - b.get_site(i)).max() == 0.0
 
 
+def test_apply_layer_uneven_bonds_matches_one_by_one():
+    """A layer over bonds 2..4096 (26 qubits, random canonical state): the gates up to
+    chi_l, chi_r = 2048 run concurrently on the layer lanes, the central ones on the
+    handle's stream; every site, the bond dims and the discarded weight equal the
+    one-by-one result exactly."""
+    n, chi = 26, 4096
+    sites = states.random_canonical_mps(n, states.max_bond_dims(n, chi), 12, seed=3)
+    rng = np.random.default_rng(21)
+    bonds = list(range(0, n - 1, 2))
+    gs = [gates.haar_unitary(rng, 4) for _ in bonds]
+    with gpu_mps(n, chi, precision="mixed", policy="local") as a, gpu_mps(n, chi, precision="mixed", policy="local") as b:
+        a.set_sites([x.astype(np.complex64) for x in sites], centre=12)
+        b.set_sites([x.astype(np.complex64) for x in sites], centre=12)
+        a.apply_layer(bonds, gs)
+        for q, g in zip(bonds, gs):
+            b.apply_2q(q, g)
+        assert a.bond_dims() == b.bond_dims()
+        assert a.discarded() == b.discarded()
+        for i in range(n):
+            assert np.array_equal(a.get_site(i, fmt="c64"), b.get_site(i, fmt="c64")), i
+
+
 def test_overlap_and_cross_precision():
     n = 10
     ops = circuits.brickwall(n, 6, seed=12)
