@@ -475,6 +475,55 @@ def layer_workload(args):
     print(json.dumps(out), flush=True)
 
 
+def circuit_workload(args):
+    """Whole circuits (the scope table's M2 and, reduced, M3 workloads), mixed and FP64
+    paths under the canonical policy: two-qubit gate applies per second of each path
+    (CUDA-synchronised wall clock over the whole circuit, routed gates counted once) and
+    the mixed-vs-FP64 fidelity deviation at the end (R15: relative norm-fidelity
+    difference and 1 - |<mix|64>|^2 / (<mix|mix><64|64>), contractions in FP64)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from workloads import circuits
+
+    __graft_entry__.build()
+    from paper_2505_06119_gb300 import MPS
+
+    if args.circuit == "config2":
+        n, chi = 40, 1024
+        ops = circuits.brickwall(n, 20, seed=7)
+        name = "40-qubit chain, depth-20 brick-wall of Haar SU(4) + SU(2), chi_max=1024, seed 7"
+    else:
+        n, chi = 49, args.grid_chi
+        ops = circuits.grid_rcs(7, 7, 12, seed=11)
+        name = ("7x7 grid random circuit snaked onto a chain, 12 cycles ABCDCDAB, paper 1q gate set and "
+                "fSim, SWAP-routed vertical couplers, chi_max=%d (reduced from 4096), seed 11" % chi)
+    n2q = circuits.count_two_qubit(ops)
+    res = {}
+    states_ = {}
+    for prec in ("mixed", "fp64"):
+        m = MPS(n, chi, precision=prec, policy="canon")
+        m.sync()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        m.run(ops)
+        m.sync()
+        dt = time.perf_counter() - t
+        res[prec] = {"seconds": dt, "two_qubit_gates_per_s": n2q / dt, "fidelity": m.fidelity(),
+                     "max_bond": max(m.bond_dims())}
+        states_[prec] = m
+    mm, m64 = states_["mixed"], states_["fp64"]
+    o = mm.overlap(m64)
+    dev_o = 1.0 - abs(o) ** 2 / (mm.overlap(mm).real * m64.overlap(m64).real)
+    dev_f = abs(res["mixed"]["fidelity"] - res["fp64"]["fidelity"]) / res["fp64"]["fidelity"]
+    for m in states_.values():
+        m.close()
+    print(json.dumps({"workload": "circuit", "circuit": name, "two_qubit_gates": n2q, "paths": res,
+                      "speedup_mixed_vs_fp64": res["fp64"]["seconds"] / res["mixed"]["seconds"],
+                      "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,12 +537,17 @@ def main():
     ap.add_argument("--cpu-chi", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-overlap", action="store_true")
-    ap.add_argument("--workload", default="gate", choices=["gate", "layer"],
-                    help="gate: the headline metric; layer: batched vs one-by-one layer times")
+    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit"],
+                    help="gate: the headline metric; layer: batched vs one-by-one layer times; "
+                         "circuit: whole-circuit throughput and fidelity deviation")
     ap.add_argument("--layer-chi", default="256,1024,2048")
+    ap.add_argument("--circuit", default="config2", choices=["config2", "grid"])
+    ap.add_argument("--grid-chi", type=int, default=256)
     args = ap.parse_args()
     if args.workload == "layer":
         layer_workload(args)
+    elif args.workload == "circuit":
+        circuit_workload(args)
     elif args.impl == "reference":
         reference(args)
     else:
