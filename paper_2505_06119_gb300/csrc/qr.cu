@@ -866,32 +866,57 @@ __device__ __forceinline__ double cp_block_sum(double v, double* s_red) {
   return t;
 }
 
+// Per step J = j0 + kk, with x = column kk below row J:
+//   partials of this CTA (computed at the end of the previous step):
+//     ||x||^2 (FP64), alpha = W[J, kk] (its owner), e_c = sum_{r > J} conj(x_r) W[r, c],
+//     W[J, c] (the owner of row J), for every panel column c;
+//   one cluster barrier; every CTA combines all partials in the same fixed order;
+//   beta, tau, sc = 1/(alpha - beta) in FP64 (warp 0) while the other warps combine e, W[J, :];
+//   d_c = v^H W[:, c] = W[J, c] + conj(sc) e_c;  c > kk: W[J:m, c] -= v conj(tau) d_c;
+//   c < kk: w_kk[c] = conj(d_c);  then the partials of step kk + 1.
 template <typename T>
 __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
   using R = typename real_of<T>::type;
   extern __shared__ __align__(16) unsigned char cp_raw[];
-  T* P = reinterpret_cast<T*>(cp_raw);  // [kb][rb], column c at P + c * rb
-  __shared__ double s_r1[2][3];          // per step: ||x_{J+1:}||^2 partial, alpha (re, im)
-  __shared__ T s_r2[2][kPanelNbMax];     // per step: partial v^H W[:, c]
-  __shared__ T s_f[kPanelNbMax];         // conj(tau) d_c
-  __shared__ T s_d[kPanelNbMax];         // reduced d_c
+  T* P = reinterpret_cast<T*>(cp_raw);   // [kb][rb], column c at P + c * rb
+  __shared__ double s_r1[2][3];           // per step: ||x||^2 partial, alpha (re, im)
+  __shared__ T s_e[2][kPanelNbMax];       // per step: partial e_c
+  __shared__ T s_j[2][kPanelNbMax];       // per step: W[J, c] (owner) or 0
+  __shared__ T s_pe[kPanelNbMax][kClusterMax + 1];  // gathered partials, combined in rank order
+  __shared__ T s_pj[kPanelNbMax][kClusterMax + 1];
+  __shared__ T s_f[kPanelNbMax];          // conj(tau) d_c
+  __shared__ T s_d[kPanelNbMax];          // d_c
   __shared__ double s_red[CPW];
-  __shared__ c128 s_sc[3];               // tau, 1/(alpha-beta), beta
+  __shared__ c128 s_sc[3];                // tau, 1/(alpha-beta), beta
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned cs = gridDim.x;          // CTAs in the cluster (one cluster)
+  const unsigned cs = gridDim.x;           // CTAs in the cluster (one cluster)
   const unsigned rank = cluster_rank();
   const int m = a.m, kb = a.kb, rb = a.rb;
   const int r0 = a.j0 + (int)rank * rb, r1 = min(m, r0 + rb);
   const int nr = max(0, r1 - r0);
-  // this CTA's contribution to the norm of column c below row J, and alpha = W[J, c]
-  auto norm_partial = [&](int c, int J, double part) {
+  // partials of the step on column c (row J): norm and alpha from `part`, e and W[J, :]
+  auto partials = [&](int c, int J, double part) {
+    const int pr = c & 1;
+    const T* x = P + c * rb;
+    const int rs = max(0, J + 1 - r0);  // first local row > J
+    for (int q = warp; q < kb; q += CPW) {
+      const T* col = P + q * rb;
+      T acc = mk<R>(0, 0);
+      for (int rr = rs + lane; rr < nr; rr += 32) cfma(acc, cconj(x[rr]), col[rr]);
+      acc.re = warp_sum(acc.re);
+      acc.im = warp_sum(acc.im);
+      if (lane == 0) {
+        s_e[pr][q] = acc;
+        s_j[pr][q] = (J >= r0 && J < r1) ? col[J - r0] : mk<R>(0, 0);
+      }
+    }
     const double t = cp_block_sum(part, s_red);
     if (tid == 0) {
       const bool own = J >= r0 && J < r1;
-      const T al = own ? P[c * rb + (J - r0)] : mk<R>(0, 0);
-      s_r1[c & 1][0] = t;
-      s_r1[c & 1][1] = (double)al.re;
-      s_r1[c & 1][2] = (double)al.im;
+      const T al = own ? x[J - r0] : mk<R>(0, 0);
+      s_r1[pr][0] = t;
+      s_r1[pr][1] = (double)al.re;
+      s_r1[pr][2] = (double)al.im;
     }
   };
   for (int c = 0; c < kb; ++c)
@@ -903,15 +928,15 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
       const T v = P[rr];
       part += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
     }
-    norm_partial(0, a.j0, part);
+    partials(0, a.j0, part);
   }
 
   for (int kk = 0; kk < kb; ++kk) {
     const int J = a.j0 + kk, par = kk & 1;
     T* x = P + kk * rb;
     cluster_sync();
-    // reflector, identical in every CTA (partials combined in the same order)
     if (warp == 0) {
+      // reflector, identical in every CTA (partials combined in the same order)
       double v0 = 0.0, v1 = 0.0, v2 = 0.0;
       if (lane < (int)cs) {
         v0 = ld_dsmem_f64(map_cta(&s_r1[par][0], lane));
@@ -944,44 +969,30 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
         s_sc[1] = sc;
         s_sc[2] = beta;
       }
+    } else {
+      // gather e_c and W[J, c] of every CTA (warps 1..)
+      for (int idx = tid - 32; idx < 2 * kb * (int)cs; idx += CPT - 32) {
+        const int arr = idx / (kb * (int)cs), rem = idx - arr * kb * (int)cs;
+        const int c = rem / (int)cs, q = rem - c * (int)cs;
+        const T* src = arr == 0 ? &s_e[par][c] : &s_j[par][c];
+        const T v = ld_dsmem(static_cast<const T*>(nullptr), map_cta(src, q));
+        if (arr == 0)
+          s_pe[c][q] = v;
+        else
+          s_pj[c][q] = v;
+      }
     }
     __syncthreads();
     const T tau = ccast<R>(s_sc[0]), sc = ccast<R>(s_sc[1]);
-    const int rs = max(0, J - r0);  // first local row >= J
-    // partial d_c = sum_{r >= J} conj(v_r) W[r, c] with v_J = 1, v_r = x_r / (alpha - beta)
-    for (int c0 = warp; c0 < kb; c0 += 2 * CPW) {
-      const int c1 = c0 + CPW;
-      const T* col0 = P + c0 * rb;
-      const T* col1 = P + min(c1, kb - 1) * rb;
-      T acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
-      for (int rr = rs + lane; rr < nr; rr += 32) {
-        const T v = cconj((r0 + rr == J) ? mk<R>(1, 0) : x[rr] * sc);
-        cfma(acc0, v, col0[rr]);
-        cfma(acc1, v, col1[rr]);
+    if (tid < kb) {
+      T e = mk<R>(0, 0), wj = mk<R>(0, 0);
+      for (int q = 0; q < (int)cs; ++q) {
+        e = e + s_pe[tid][q];
+        wj = wj + s_pj[tid][q];
       }
-      acc0.re = warp_sum(acc0.re);
-      acc0.im = warp_sum(acc0.im);
-      acc1.re = warp_sum(acc1.re);
-      acc1.im = warp_sum(acc1.im);
-      if (lane == 0) {
-        s_r2[par][c0] = acc0;
-        if (c1 < kb) s_r2[par][c1] = acc1;
-      }
-    }
-    cluster_sync();
-    // d_c summed over the cluster (16 lanes per column)
-    {
-      const int c = tid / kClusterMax, q = tid % kClusterMax;
-      T v = mk<R>(0, 0);
-      if (c < kb && q < (int)cs) v = ld_dsmem(static_cast<const T*>(nullptr), map_cta(&s_r2[par][c], q));
-      for (int o = 1; o < kClusterMax; o <<= 1) {
-        v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
-        v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
-      }
-      if (c < kb && q == 0) {
-        s_d[c] = v;
-        s_f[c] = cconj(tau) * v;
-      }
+      const T d = wj + cconj(sc) * e;  // v^H W[:, c]
+      s_d[tid] = d;
+      s_f[tid] = cconj(tau) * d;
     }
     __syncthreads();
     if (rank == 0) {
@@ -990,6 +1001,7 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
     }
     // v stored in place of x; trailing panel columns W[J:m, c] -= v conj(tau) d_c;
     // the next column's norm below row J+1 is accumulated on the way
+    const int rs = max(0, J - r0);  // first local row >= J
     double part = 0.0;
     for (int rr = rs + tid; rr < nr; rr += CPT) {
       const int r = r0 + rr;
@@ -1006,8 +1018,8 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
       }
     }
     if (J >= r0 && J < r1 && tid == 0) x[J - r0] = ccast<R>(s_sc[2]);  // R diagonal
-    if (kk + 1 < kb) norm_partial(kk + 1, J + 1, part);  // contains __syncthreads
     __syncthreads();
+    if (kk + 1 < kb) partials(kk + 1, J + 1, part);  // contains __syncthreads
   }
   cluster_sync();  // no CTA leaves while another may still read its shared memory
   for (int c = 0; c < kb; ++c)
