@@ -95,6 +95,25 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
     kbeg = blockIdx.z * per;
     kend = min(d.K, kbeg + per);
   }
+  // triangular operands: K ranges where the mask zeroes the whole tile row/column
+  // block contribute nothing and are skipped (the sums are unchanged: only exact
+  // zero products are left out)
+  if (d.a_mask == MASK_UPPER) {
+    if (d.a_row) kend = min(kend, i0 + BM);
+    else kbeg = max(kbeg, i0);
+  } else if (d.a_mask == MASK_UNIT_LOWER) {
+    if (d.a_row) kbeg = max(kbeg, i0);
+    else kend = min(kend, i0 + BM);
+  }
+  if (!THETA) {
+    if (d.b_mask == MASK_UPPER) {
+      if (d.b_row) kbeg = max(kbeg, j0);
+      else kend = min(kend, j0 + G_BN);
+    } else if (d.b_mask == MASK_UNIT_LOWER) {
+      if (d.b_row) kend = min(kend, j0 + G_BN);
+      else kbeg = max(kbeg, j0);
+    }
+  }
   constexpr bool beta_nz = BETA && !THETA;  // the host launches BETA only without split-K
   const bool fix_a = d.a_conj || d.a_mask == MASK_UNIT_LOWER;
   const bool fix_b = d.b_conj || d.b_mask == MASK_UNIT_LOWER;
