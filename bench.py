@@ -524,6 +524,64 @@ def circuit_workload(args):
                       "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o}}), flush=True)
 
 
+def big_gate_workload(args):
+    """One two-site apply at the paper's largest bond dimension (chi_l = chi_m = chi_r =
+    args.big_chi, theta (2 chi)^2; the scope table's M5 timing), mixed path, through the
+    raw-pointer C call on device buffers: Gaussian sites made on the GPU, seeded.  Checks
+    the norm identity ||R P^T||^2 + discarded = ||theta||^2 with ||theta||^2 =
+    sum (A^H A) .* conj(B B^H) (the gate is unitary on the physical indices)."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from workloads import gates
+
+    __graft_entry__.build()
+    from paper_2505_06119_gb300 import _lib as L
+    from paper_2505_06119_gb300.mps import _gate
+
+    lib = L.load()
+    chi = args.big_chi
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+
+    def site():
+        x = torch.randn((chi, 2, chi), dtype=torch.complex64, device=dev, generator=gen)
+        return x / torch.linalg.vector_norm(x)
+
+    a, b = site(), site()
+    g = gates.haar_unitary(np.random.default_rng(5), 4)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    A2 = a.reshape(2 * chi, chi)
+    B2 = b.reshape(chi, 2 * chi)
+    theta2 = float(((A2.conj().T @ A2) * (B2 @ B2.conj().T).conj()).sum().real)
+    sz = ctypes.c_size_t()
+    code = L.MPS_PREC_MIXED
+    assert lib.mps_two_site_workspace(code, chi, chi, chi, chi, ctypes.byref(sz)) == 0
+    ws = torch.empty(sz.value + 256, dtype=torch.uint8, device=dev)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    disc = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rc = lib.mps_two_site_apply(code, chi, chi, chi, chi, a.data_ptr(), b.data_ptr(), _gate(g, 16), a.data_ptr(),
+                                b.data_ptr(), disc.data_ptr(), base, sz.value, stream)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kept = float((b.abs() ** 2).sum())
+    flops = 82.7 * chi ** 3
+    print(json.dumps({"workload": "big_gate", "chi": chi, "theta": "%d x %d complex64" % (2 * chi, 2 * chi),
+                      "rc": rc, "seconds": ms / 1e3, "applies_per_s": 1e3 / ms,
+                      "tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
+                      "workspace_gib": sz.value / 2 ** 30,
+                      "norm_identity_rel": abs(kept + disc.item() - theta2) / theta2}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,9 +595,11 @@ def main():
     ap.add_argument("--cpu-chi", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-overlap", action="store_true")
-    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit"],
+    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit", "big"],
                     help="gate: the headline metric; layer: batched vs one-by-one layer times; "
-                         "circuit: whole-circuit throughput and fidelity deviation")
+                         "circuit: whole-circuit throughput and fidelity deviation; "
+                         "big: one apply at a large bond dimension")
+    ap.add_argument("--big-chi", type=int, default=16384)
     ap.add_argument("--layer-chi", default="256,1024,2048")
     ap.add_argument("--circuit", default="config2", choices=["config2", "grid"])
     ap.add_argument("--grid-chi", type=int, default=256)
@@ -548,6 +608,8 @@ def main():
         layer_workload(args)
     elif args.workload == "circuit":
         circuit_workload(args)
+    elif args.workload == "big":
+        big_gate_workload(args)
     elif args.impl == "reference":
         reference(args)
     else:

@@ -109,7 +109,10 @@ typedef struct {
   int debug_barrier_extra; /* testing only, normally 0: a grid barrier waits for this many
                               arrivals that never come, so every bounded wait expires and
                               the call fails with MPS_E_TIMEOUT instead of hanging */
-  int reserved[7];
+  int debug_max_ctas;     /* testing only, normally 0: caps the CTAs of the cooperative QR
+                             panel kernel so that small matrices take the paths of large
+                             ones (more than 128 rows per CTA); negative: MPS_E_ARG */
+  int reserved[6];
 } mps_config;
 
 /* Fill *cfg with the defaults listed above. */

@@ -47,7 +47,8 @@ class mps_config(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("panel_width", ctypes.c_int),
                 ("wait_timeout_s", ctypes.c_double), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("flags", ctypes.c_int),
-                ("debug_barrier_extra", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("debug_barrier_extra", ctypes.c_int), ("debug_max_ctas", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class mps_kstat(ctypes.Structure):

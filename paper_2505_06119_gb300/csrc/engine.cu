@@ -989,6 +989,7 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   if (cfg.panel_width < 0 || cfg.panel_width > kMaxNb) return MPS_E_ARG;
   if ((cfg.alloc == nullptr) != (cfg.free == nullptr)) return MPS_E_ARG;
   if (cfg.wait_timeout_s < 0) return MPS_E_ARG;
+  if (cfg.debug_barrier_extra < 0 || cfg.debug_max_ctas < 0) return MPS_E_ARG;
   mps_s* h = new (std::nothrow) mps_s();
   if (!h) return MPS_E_NOMEM;
   h->n = n;
@@ -1004,9 +1005,6 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   h->kn.flag_tol = h->prec == MPS_PREC_FP64 ? 1.4901161193847656e-08 : 1e-3;
   double to = cfg.wait_timeout_s > 0 ? cfg.wait_timeout_s : 10.0;
   h->kn.timeout_ns = (unsigned long long)(to * 1e9);
-  if (cfg.debug_barrier_extra < 0) {
-    return MPS_E_ARG;
-  }
   h->kn.barrier_extra = (unsigned)cfg.debug_barrier_extra;
   h->prof.enabled = (cfg.flags & MPS_FLAG_PROFILE) != 0;
   h->kn.use_tc = h->prec == MPS_PREC_MIXED && (cfg.flags & MPS_FLAG_TENSOR_CORES) != 0;
@@ -1026,6 +1024,7 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   }
   int sms = num_sms();
   h->kn.G = std::min(sms, kMaxCoop);
+  if (cfg.debug_max_ctas > 0) h->kn.G = std::min(h->kn.G, cfg.debug_max_ctas);
   if (cfg.stream) {
     h->stream = (cudaStream_t)cfg.stream;
   } else {

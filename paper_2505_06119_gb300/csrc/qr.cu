@@ -434,56 +434,65 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       int u0, u1;
       split_range(J, m, gb, b, u0, u1);
       const int sub = tid & 3;
-      const int r = u0 + (tid >> 2);
-      const bool act = r < u1;
       constexpr int U = kPanelNbMax / 4;
-      T vr[U], fp[U];
-      // issue every load of this phase before using any
+      T fp[U], cs[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int i = sub + 4 * u;
-        vr[u] = mk<R>(0, 0);
-        fp[u] = mk<R>(0, 0);
-        if (i < kk) {
-          fp[u] = a.F[(int64_t)p * nb + i];
-          if (act) vr[u] = W[r + (int64_t)(a.j0 + i) * ldw];
+        fp[u] = (i < kk) ? a.F[(int64_t)p * nb + i] : mk<R>(0, 0);
+        cs[u] = mk<R>(0, 0);
+      }
+      double nrm = 0.0;
+      // 128 rows per pass (more than one pass only when m - J > 128 G)
+      for (int rb = u0; rb < u1; rb += PNT / 4) {
+        const int r = rb + (tid >> 2);
+        const bool act = r < u1;
+        T vr[U];
+        // issue every load of this pass before using any
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = sub + 4 * u;
+          vr[u] = mk<R>(0, 0);
+          if (i < kk && act) vr[u] = W[r + (int64_t)(a.j0 + i) * ldw];
+        }
+        T cj = mk<R>(0, 0), cp = mk<R>(0, 0);
+        if (act && sub == 0) {
+          cj = colJ[r];
+          cp = colP[r];
+        }
+        if (kk > 0 && act && sub == ((kk - 1) & 3)) {  // previous reflector: rows > J-1, scaled once
+          const int u = (kk - 1) >> 2;
+          const T scp = ccast<R>(s_prev);
+#pragma unroll
+          for (int uu = 0; uu < U; ++uu)
+            if (uu == u) {
+              vr[uu] = vr[uu] * scp;
+              W[r + (int64_t)(J - 1) * ldw] = vr[uu];
+            }
+        }
+        T x = (sub == 0) ? ((p != J) ? cp : cj) : mk<R>(0, 0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) x = x - vr[u] * cconj(fp[u]);
+        x.re += __shfl_xor_sync(0xffffffffu, x.re, 1);
+        x.im += __shfl_xor_sync(0xffffffffu, x.im, 1);
+        x.re += __shfl_xor_sync(0xffffffffu, x.re, 2);
+        x.im += __shfl_xor_sync(0xffffffffu, x.im, 2);
+        if (act && sub == 0) {
+          colJ[r] = x;
+          if (p != J) colP[r] = cj;
+          if (r > J) nrm += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
+          if (r == J) *a.alpha_slot = ccast<double>(x);
+        }
+        // partial w_i = sum_{rows > J} conj(V[r, i]) x_r
+        if (act && r > J) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) cs[u] = cs[u] + cconj(vr[u]) * x;
         }
       }
-      T cj = mk<R>(0, 0), cp = mk<R>(0, 0);
-      if (act && sub == 0) {
-        cj = colJ[r];
-        cp = colP[r];
-      }
-      if (kk > 0 && act && sub == ((kk - 1) & 3)) {  // previous reflector: rows > J-1, scaled once
-        const int u = (kk - 1) >> 2;
-        const T scp = ccast<R>(s_prev);
-#pragma unroll
-        for (int uu = 0; uu < U; ++uu)
-          if (uu == u) {
-            vr[uu] = vr[uu] * scp;
-            W[r + (int64_t)(J - 1) * ldw] = vr[uu];
-          }
-      }
-      T x = (sub == 0) ? ((p != J) ? cp : cj) : mk<R>(0, 0);
-#pragma unroll
-      for (int u = 0; u < U; ++u) x = x - vr[u] * cconj(fp[u]);
-      x.re += __shfl_xor_sync(0xffffffffu, x.re, 1);
-      x.im += __shfl_xor_sync(0xffffffffu, x.im, 1);
-      x.re += __shfl_xor_sync(0xffffffffu, x.re, 2);
-      x.im += __shfl_xor_sync(0xffffffffu, x.im, 2);
-      double nrm = 0.0;
-      if (act && sub == 0) {
-        colJ[r] = x;
-        if (p != J) colP[r] = cj;
-        if (r > J) nrm = (double)x.re * (double)x.re + (double)x.im * (double)x.im;
-        if (r == J) *a.alpha_slot = ccast<double>(x);
-      }
-      // partial w_i = sum_{rows > J} conj(V[r, i]) x_r: reduce over the 8 rows of the warp
-      const bool below = act && r > J;
+      // reduce over the 8 rows of the warp
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        T c = mk<R>(0, 0);
-        if (below) c = cconj(vr[u]) * x;
+        T c = cs[u];
         c.re += __shfl_xor_sync(0xffffffffu, c.re, 4);
         c.im += __shfl_xor_sync(0xffffffffu, c.im, 4);
         c.re += __shfl_xor_sync(0xffffffffu, c.re, 8);

@@ -29,7 +29,7 @@ def _gate(g, n):
 
 
 def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile=False,
-           wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False):
+           wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False, debug_max_ctas=0):
     lib = L.load()
     cfg = L.mps_config()
     lib.mps_config_init(ctypes.byref(cfg))
@@ -41,6 +41,7 @@ def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile
     cfg.wait_timeout_s = wait_timeout_s
     cfg.device = device
     cfg.debug_barrier_extra = debug_barrier_extra
+    cfg.debug_max_ctas = debug_max_ctas
     return cfg
 
 

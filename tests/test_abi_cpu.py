@@ -62,6 +62,12 @@ def test_host_argument_checks(lib):
     lib.mps_config_init(ctypes.byref(cfg))
     cfg.panel_width = 33
     assert lib.mps_create_ex(ctypes.byref(h), 4, 4, ctypes.byref(cfg)) == L.MPS_E_ARG
+    lib.mps_config_init(ctypes.byref(cfg))
+    cfg.debug_max_ctas = -1
+    assert lib.mps_create_ex(ctypes.byref(h), 4, 4, ctypes.byref(cfg)) == L.MPS_E_ARG
+    lib.mps_config_init(ctypes.byref(cfg))
+    cfg.debug_barrier_extra = -1
+    assert lib.mps_create_ex(ctypes.byref(h), 4, 4, ctypes.byref(cfg)) == L.MPS_E_ARG
     assert lib.mps_destroy(None) == L.MPS_OK
     assert lib.mps_apply_2q(None, 0, None, 4) == L.MPS_E_ARG
     assert lib.mps_version() >= 100

@@ -77,8 +77,13 @@ SPLIT_CASES = [
 ]
 
 
-@pytest.mark.parametrize("cl,cm,cr,chi", SPLIT_CASES)
-def test_single_split_fp64_matches_oracle(cl, cm, cr, chi):
+# (cl, cm, cr, chi, max_ctas): max_ctas > 0 caps the panel kernel's grid so that each
+# CTA owns more than 128 rows of theta, the regime of chi above ~9700 on the full GPU
+SPLIT_CASES_CAPPED = [(257, 64, 200, 160, 2), (300, 80, 300, 300, 1)]
+
+
+@pytest.mark.parametrize("cl,cm,cr,chi,max_ctas", [c + (0,) for c in SPLIT_CASES] + SPLIT_CASES_CAPPED)
+def test_single_split_fp64_matches_oracle(cl, cm, cr, chi, max_ctas):
     """One two-site apply on saturated random sites: new sites equal the oracle's
     Q and R P^T element by element (tie-free Gaussian input, LOCAL policy so no
     centre move is involved)."""
@@ -88,7 +93,7 @@ def test_single_split_fp64_matches_oracle(cl, cm, cr, chi):
     g = gates.haar_unitary(rng, 4)
     n, i = placement(cl, cm, cr)
     chi_cap = max(cl, cm, cr, chi, 4)
-    with gpu_mps(n, chi_cap, precision="fp64", policy="local") as m:
+    with gpu_mps(n, chi_cap, precision="fp64", policy="local", debug_max_ctas=max_ctas) as m:
         load_two_sites(m, i, a, b)
         m.apply_2q(i, g, chi)
         qa = m.get_site(i)
