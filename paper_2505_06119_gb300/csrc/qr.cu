@@ -50,7 +50,7 @@ constexpr int kDChMax = 32;      // row chunks per column in phase D (about 8 KB
 constexpr int kDpCap = kDBatch * kDChMax;  // phase-D chunk sums held at once
 constexpr int kSlot = 4096;      // bytes of one bulk-copy slot (phase D, bulk mode)
 constexpr int kRing = PNW * 2 * kSlot;  // two slots per warp
-constexpr int kNSW = 2;                 // warps on the reflector scalars in bulk mode
+constexpr int kNSW = 1;                 // warps on the reflector scalars in bulk mode
 constexpr int kNDW = PNW - kNSW;        // warps on the trailing sweep in bulk mode
 
 template <typename T>
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
 
     // ---------------- C: reflector (every CTA, identical FP64 arithmetic).
-    // Warp 0 computes beta, tau and 1/(alpha - beta) in FP64; warp 1 combines the
+    // Warp 0 computes beta, tau and 1/(alpha - beta) in FP64, then combines the
     // CTAs' partial sums of V^H x.  In bulk mode x is staged by one bulk copy and
     // the other warps go straight on to the trailing sweep (phase D1), which needs
     // only x; the reflector scalars are first used in the D2 epilogue.
@@ -568,7 +568,8 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         s_scal[1] = sc;
         s_scal[2] = beta;
       }
-    } else if (warp == 1 && lane < kk) {
+    }
+    if (warp == 0 && lane < kk) {
       // lane i: sum over the CTAs of V_i^H x (below row J), in CTA order; row J of V
       T acc = mk<R>(0, 0);
       int g = 0;
