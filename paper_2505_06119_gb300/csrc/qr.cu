@@ -648,7 +648,8 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           if (lane == 0 && li + 2 < nli) {
             const int it2 = it + 2 * kNDW, cl2 = it2 / nchb, ch2 = it2 - cl2 * nchb;
             const int cs2 = xbase + ch2 * CR, ce2 = min(m, cs2 + CR);
-            fence_proxy_async();  // this slot's reads before the next asynchronous write into it
+            // the slot's previous contents were consumed above (values in registers,
+            // __syncwarp passed), so the copy cannot overtake those reads
             mbar_expect_tx(mb, (uint32_t)((ce2 - cs2) * sizeof(T)));
             bulk_g2s(smem_u32(slot0 + q * kSlot), W + (int64_t)(cb + cl2) * ldw + cs2,
                      (uint32_t)((ce2 - cs2) * sizeof(T)), mb);
@@ -794,7 +795,8 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       xph ^= 1u;
     }
     s_prev = s_scal[1];
-    if (a.bulk) fence_proxy_async();  // this step's generic writes before later bulk reads
+    // (no proxy fence here: what this step wrote with plain stores, row J and the
+    // panel's own columns, is not read by a bulk copy before the next phase-B fence)
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
   }
   // final deferred scaling of the panel's last reflector, rows > Jl
