@@ -443,6 +443,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         cs[u] = mk<R>(0, 0);
       }
       double nrm = 0.0;
+      bool wrote = false;  // this thread stored rows >= J of columns J / p (read later by bulk copies)
       // 128 rows per pass (more than one pass only when m - J > 128 G)
       for (int rb = u0; rb < u1; rb += PNT / 4) {
         const int r = rb + (tid >> 2);
@@ -480,6 +481,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         if (act && sub == 0) {
           colJ[r] = x;
           if (p != J) colP[r] = cj;
+          wrote = true;
           if (r > J) nrm += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
           if (r == J) *a.alpha_slot = ccast<double>(x);
         }
@@ -489,6 +491,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           for (int u = 0; u < U; ++u) cs[u] = cs[u] + cconj(vr[u]) * x;
         }
       }
+      if (a.bulk && wrote) fence_proxy_async();  // these stores before the bulk reads of phase C/D
       // reduce over the 8 rows of the warp
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -514,7 +517,6 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       a.jpvt[J] = a.jpvt[p];
       a.jpvt[p] = t0;
     }
-    if (a.bulk) fence_proxy_async();  // phase-B writes (column swap) before later bulk reads
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
 
     // ---------------- C: reflector (every CTA, identical FP64 arithmetic).
