@@ -125,7 +125,7 @@ struct QrPlan {
   int* jpvt;       // n
   T* Tfac;         // ceil(k/nb) * nb * nb, per-panel triangular factors (column-major nb x nb)
   c128* Wg;        // ceil(k/nb) * nb * nb, per-step w = V^H v saved by the panel kernel
-  T* F;            // n x nb row-major (ld nb)
+  T* F;            // n x nb row-major (ld nb): conj of the QP3 matrix F, so W -= V F^H reads it plainly
   double* vn1;     // n
   double* vn2;     // n
   // reduction scratch for the cooperative panel kernel

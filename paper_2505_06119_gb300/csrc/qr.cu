@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         }
         T x = (sub == 0) ? ((p != J) ? cp : cj) : mk<R>(0, 0);
 #pragma unroll
-        for (int u = 0; u < U; ++u) x = x - vr[u] * cconj(fp[u]);
+        for (int u = 0; u < U; ++u) x = x - vr[u] * fp[u];  // F stored conjugated
         x.re += __shfl_xor_sync(0xffffffffu, x.re, 1);
         x.im += __shfl_xor_sync(0xffffffffu, x.im, 1);
         x.re += __shfl_xor_sync(0xffffffffu, x.re, 2);
@@ -708,11 +708,12 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         const T wJt = wJtT[q];
         const T y = cconj(wJt) + sc * acc;
         // F[t, kk] = tau * (y - sum_i F[src, i] w_i); row update of W[J, t]
+        // (the array holds conj(F): the trailing update reads it as F^H directly)
         T fw = mk<R>(0, 0), rowu = mk<R>(0, 0);
         if (lane < kk) {
-          const T fi = fiT[q];
-          cfma(fw, fi, w_l);
-          cfma(rowu, s_vrow[lane], cconj(fi));
+          const T fi = fiT[q];  // conj(F[src, lane])
+          cfma(fw, cconj(fi), w_l);
+          cfma(rowu, s_vrow[lane], fi);
           if (t == p) Ft[lane] = fi;
         }
         fw.re = warp_sum(fw.re);
@@ -724,7 +725,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         double v1 = v1a[q], v2 = v2a[q];
         int need = 0;
         if (lane == 0) {
-          Ft[kk] = f;
+          Ft[kk] = cconj(f);
           W[J + (int64_t)t * ldw] = wnew;
           if (a.pivot) {
             if (L <= 0) {
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
             c128 z = ccast<double>(col[r]);
             for (int i = 0; i < kk; ++i) {
               c128 vv = ccast<double>(W[r + (int64_t)(a.j0 + i) * ldw]);
-              z = z - vv * cconj(ccast<double>(Fs[i]));
+              z = z - vv * ccast<double>(Fs[i]);  // Fs holds conj(F)
             }
             c128 vx = scd * ccast<double>(colJ[r]);
             z = z - vx * cf;
@@ -1552,10 +1553,10 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
         d.a_row = 0;
         d.a_conj = 0;
         d.a_mask = MASK_NONE;
-        d.B = p.F + (int64_t)J1 * nb;  // B(k, j) = conj(F[J1 + j, k]) -> stored col-major, ld nb
+        d.B = p.F + (int64_t)J1 * nb;  // B(k, j) = conj(F[J1 + j, k]): the array holds conj(F), col-major, ld nb
         d.ldb = nb;
         d.b_row = 0;
-        d.b_conj = 1;
+        d.b_conj = 0;
         d.b_mask = MASK_NONE;
         d.C = p.W + J1 + (int64_t)J1 * p.ldw;
         d.ldc = p.ldw;
