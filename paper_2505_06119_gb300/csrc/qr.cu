@@ -610,6 +610,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     const int nbc = a.bulk ? max(1, min(kDBatch, kDpCap / max(nchb, 1))) : kDBatch;
     if (a.bulk && lane == 0) fence_proxy_async();  // generic writes before the barrier -> async reads
     bool xseen = false;
+    bool pre = false;  // bulk mode: this batch's first two items were issued during the previous one
     for (int cb = c0; cb < c1; cb += nbc) {
       const int nc = min(nbc, c1 - cb);
       // D1: chunk sums
@@ -624,16 +625,21 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
             mbar_wait_plain(smem_u32(&s_xbar), xph, a.timeout_ns);
           xseen = true;
         }
-        if (lane == 0) {
-          for (int li = 0; li < min(2, nli); ++li) {
+        // first two items of batch cb0 (nc0 columns) into slots 0 and 1
+        auto prologue = [&](int cb0, int nc0) {
+          const int nit0 = nc0 * nchb;
+          const int nli0 = (dw >= 0 && nit0 > dw) ? (nit0 - dw + kNDW - 1) / kNDW : 0;
+          for (int li = 0; li < min(2, nli0); ++li) {
             const int it = dw + kNDW * li, cl = it / nchb, ch = it - cl * nchb;
             const int cs = xbase + ch * CR, ce = min(m, cs + CR);
             const uint32_t mb = smem_u32(&s_mbar[warp][li]);
             mbar_expect_tx(mb, (uint32_t)((ce - cs) * sizeof(T)));
-            bulk_g2s(smem_u32(slot0 + li * kSlot), W + (int64_t)(cb + cl) * ldw + cs, (uint32_t)((ce - cs) * sizeof(T)),
-                     mb);
+            bulk_g2s(smem_u32(slot0 + li * kSlot), W + (int64_t)(cb0 + cl) * ldw + cs,
+                     (uint32_t)((ce - cs) * sizeof(T)), mb);
           }
-        }
+        };
+        if (lane == 0 && !pre) prologue(cb, nc);
+        pre = false;
         for (int li = 0; li < nli; ++li) {
           const int q = li & 1;
           const int it = dw + kNDW * li, cl = it / nchb, ch = it - cl * nchb;
@@ -656,6 +662,12 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
             bulk_g2s(smem_u32(slot0 + q * kSlot), W + (int64_t)(cb + cl2) * ldw + cs2,
                      (uint32_t)((ce2 - cs2) * sizeof(T)), mb);
           }
+        }
+        // every slot of this warp is free again: start the next batch's copies now,
+        // so they are in flight during this batch's epilogue
+        if (cb + nbc < c1) {
+          if (lane == 0) prologue(cb + nbc, min(nbc, c1 - cb - nbc));
+          pre = true;
         }
       } else {
         for (int it = warp; it < nc * nch; it += PNW) {
