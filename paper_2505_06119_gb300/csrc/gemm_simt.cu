@@ -339,20 +339,23 @@ cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s) {
 template <typename T>
 cudaError_t theta_gemm_simt(int chi_l, int chi_m, int chi_r, const T* A, const T* B, const T* g16,
                             T* W, int64_t ldw, cudaStream_t s) {
-  if constexpr (std::is_same<T, c64>::value) return theta_c64(chi_l, chi_m, chi_r, A, B, g16, W, ldw, s);
-  ThetaArgs<T> p;
-  p.cl = chi_l;
-  p.cm = chi_m;
-  p.cr = chi_r;
-  p.A = A;
-  p.B = B;
-  for (int i = 0; i < 16; ++i) p.g[i] = g16[i];
-  p.W = W;
-  p.ldw = ldw;
-  dim3 grid((chi_l + TL - 1) / TL, (chi_r + TR - 1) / TR);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  theta_kernel<T><<<grid, NT, 0, s>>>(p);
-  return cudaGetLastError();
+  if constexpr (std::is_same<T, c64>::value) {
+    return theta_c64(chi_l, chi_m, chi_r, A, B, g16, W, ldw, s);
+  } else {
+    ThetaArgs<T> p;
+    p.cl = chi_l;
+    p.cm = chi_m;
+    p.cr = chi_r;
+    p.A = A;
+    p.B = B;
+    for (int i = 0; i < 16; ++i) p.g[i] = g16[i];
+    p.W = W;
+    p.ldw = ldw;
+    dim3 grid((chi_l + TL - 1) / TL, (chi_r + TR - 1) / TR);
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    theta_kernel<T><<<grid, NT, 0, s>>>(p);
+    return cudaGetLastError();
+  }
 }
 
 template <typename T>
