@@ -495,10 +495,11 @@ def circuit_workload(args):
         ops = circuits.brickwall(n, 20, seed=7)
         name = "40-qubit chain, depth-20 brick-wall of Haar SU(4) + SU(2), chi_max=1024, seed 7"
     else:
-        n, chi = 49, args.grid_chi
-        ops = circuits.grid_rcs(7, 7, 12, seed=11)
-        name = ("7x7 grid random circuit snaked onto a chain, 12 cycles ABCDCDAB, paper 1q gate set and "
-                "fSim, SWAP-routed vertical couplers, chi_max=%d (reduced from 4096), seed 11" % chi)
+        rows, cols, cyc = (int(x) for x in args.grid.split("x"))
+        n, chi = rows * cols, args.grid_chi
+        ops = circuits.grid_rcs(rows, cols, cyc, seed=11)
+        name = ("%dx%d grid random circuit snaked onto a chain, %d cycles ABCDCDAB, paper 1q gate set and "
+                "fSim, SWAP-routed vertical couplers, chi_max=%d, seed 11" % (rows, cols, cyc, chi))
     n2q = circuits.count_two_qubit(ops)
     res = {}
     states_ = {}
@@ -603,6 +604,7 @@ def main():
     ap.add_argument("--layer-chi", default="256,1024,2048")
     ap.add_argument("--circuit", default="config2", choices=["config2", "grid"])
     ap.add_argument("--grid-chi", type=int, default=256)
+    ap.add_argument("--grid", default="7x7x12", help="rows x cols x cycles of the grid circuit")
     args = ap.parse_args()
     if args.workload == "layer":
         layer_workload(args)
