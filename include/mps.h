@@ -147,9 +147,16 @@ int mps_swap(mps_t h, int site, int chi_max);
 int mps_apply_2q_routed(mps_t h, int q1, int q2, const mps_c128 g[16], int chi_max);
 
 /* All two-qubit gates of one circuit layer, on pairwise disjoint bonds
- * sites[j], sites[j]+1 (gates[16*j .. 16*j+15]).  Requires
- * MPS_POLICY_LOCAL (no centre moves, so the gates commute exactly and the
- * result equals applying them one by one). */
+ * sites[j], sites[j]+1 (gates[16*j .. 16*j+15]) (the gates of a brick-wall
+ * layer, Sec. III-D; network parallelism, Sec. I).  Requires MPS_POLICY_LOCAL
+ * (no centre moves, so the gates commute exactly).  Gates whose two-site block
+ * is at most 4096 x 4096 run concurrently on eight internal streams, each with
+ * its own workspace (allocated through the handle's allocator at the first
+ * call, about 8 x the workspace of a chi = 2048 split); larger ones run in
+ * order on the handle's stream, which waits for all of them before returning.
+ * The result equals applying the gates one by one, bit for bit; with
+ * MPS_FLAG_PROFILE the gates run one by one.  Asynchronous; errors as for
+ * mps_apply_2q.  chi_max as for mps_apply_2q. */
 int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count, int chi_max);
 
 /* <bits|psi> = A_0[:, b_0, :] A_1[:, b_1, :] ... (bits[i] in {0,1} for site i).
