@@ -242,17 +242,9 @@ def ours(args):
     if args.e2e_steps > 0:
         e2e = e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np)
 
-    steps_all = args.steps * ws
-    t_max = ms
-    e2e_v = e2e["value"]
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms, e2e["seconds"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_s = float(t[0]), float(t[1])
-        e2e_v = e2e["steps"] * ws / e2e_s if e2e["steps"] else None
-    value = steps_all / (t_max * 1e-3)
+    agg = replica_throughput(ms, e2e["seconds"], args.steps, e2e["steps"], ws, device="cuda")
+    t_max, value = agg["t_max_ms"], agg["value"]
+    e2e_v = agg["e2e_value"] if ws > 1 else e2e["value"]
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -302,6 +294,24 @@ def ours(args):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def replica_throughput(ms, e2e_seconds, steps, e2e_steps, ws, device="cuda"):
+    """Whole-job throughput of ws independent replicas (no data-path collective):
+    every rank timed `steps` steps in `ms` milliseconds; the job takes the slowest
+    rank's time, so value = steps * ws / max_rank(ms).  Same for the end-to-end loop.
+    One all-reduce (MAX) of the two times when ws > 1 (NCCL on "cuda", gloo on "cpu")."""
+    import torch
+
+    t_max, e2e_s = float(ms), float(e2e_seconds)
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([t_max, e2e_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_s = float(t[0]), float(t[1])
+    return {"t_max_ms": t_max, "value": steps * ws / (t_max * 1e-3),
+            "e2e_value": (e2e_steps * ws / e2e_s) if e2e_steps else None}
 
 
 def do_step_at(m, st, i):
