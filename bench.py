@@ -145,7 +145,7 @@ class ClockSampler:
 # algorithmic bytes (both are sums over the trailing block), so a launch's traffic is
 # this ratio times its algorithmic bytes.  Valid only for the kernel source it was
 # measured on (sha256 of csrc/qr.cu); otherwise reported as null.
-PANEL_NCU = {"qr_cu_sha256": "4c1f8233befe64115fa8b6f48f74ecc0d40398a1f84f3835bfb3d709d57cc6d2",
+PANEL_NCU = {"qr_cu_sha256": "8dfeb07d03c8b49c09dc2370a6ace3b1756c8f93a9ec26926d430f3cd56a2d2c",
              "dram_over_algorithmic": 0.9885}
 
 

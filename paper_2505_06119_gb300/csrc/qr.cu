@@ -12,28 +12,33 @@
 //        earlier reflectors, x = W[J:m, J] - V F[p,:]^H; partial sums of
 //        ||x_{J+1:}||^2 (FP64) and V^H x;
 //     C. reflector: beta = -sign(Re alpha) ||x||, tau = (beta - alpha)/beta,
-//        v = (1, x_{J+1:} / (alpha - beta)), in FP64;
-//     D. for every trailing column t (split across CTAs, one warp per column):
-//        y_t = W[J:m, t]^H v (the BLAS-2 sweep over the trailing matrix),
-//        F[t, k] = tau (y_t - F[t, :k] w) with w = V^H v,
-//        row update W[J, t] -= W[J, panel] F[t, :]^H (this row is final R),
-//        FP64 downdate of the squared norm, vn1[t] -= |W[J, t]|^2, with an
-//        exact recompute when vn1[t] <= tol * vn2[t] (vn2 = the last exact
-//        value), the accuracy criterion of LAPACK's xLAQPS.
+//        v = (1, x_{J+1:} / (alpha - beta)), in FP64 (one warp, overlapped
+//        with D1, which needs only x);
+//     D. for every trailing column t (columns split across CTAs):
+//        D1: y_t = W[J:m, t]^H x, the BLAS-2 sweep over the trailing matrix,
+//            streamed in 4 KB (column, row-chunk) pieces by bulk asynchronous
+//            copies into shared memory (cp.async.bulk + mbarrier);
+//        D2: F[t, k] = tau (y_t - F[t, :k] w) with w = V^H v,
+//            row update W[J, t] -= W[J, panel] F[t, :]^H (this row is final R),
+//            FP64 downdate of the squared norm, vn1[t] -= |W[J, t]|^2, with an
+//            exact recompute when vn1[t] <= tol * vn2[t] (vn2 = the last exact
+//            value), the accuracy criterion of LAPACK's xLAQPS.
 //   The data path (F, the row update, V^H v) runs in the data precision;
 //   FP64 carries the norms, the reflector norm / beta / tau and the pivots.
-//   Two grid barriers per step, every wait bounded.
+//   F is stored conjugated.  Two grid barriers per step, every wait bounded.
 //
-//   trailing update: W[J1:m, J1:n] -= V F^H (rank-nb GEMM), then an exact FP64
+//   trailing update: W[J1:m, J1:n] -= V F^H (rank-nb GEMM), then an exact
 //   recompute of every trailing column norm.
 //
-// Without pivoting (centre moves, Sec. III-C.1) the panel kernel only touches
-// the panel's own columns and the rest of the matrix receives the compact-WY
-// block reflector, C -= V T^H V^H C.
+// Without pivoting (centre moves, Sec. III-C.1) the panel only touches its own
+// columns; when it fits, it runs on one 16-CTA thread-block cluster with the
+// panel resident in shared memory (qr_cpanel_kernel).  Pairs of panels form
+// 64-column blocks whose compact-WY reflector C -= V T^H V^H C updates the rest
+// of the matrix.
 //
-// Q[:, :k] = H_0 ... H_{k-1} I is formed backwards panel by panel with the
-// triangular factors T accumulated by the panel kernel (H_j0..H_j0+kb-1 =
-// I - V T V^H).
+// Q[:, :k] = H_0 ... H_{k-1} I is formed backwards block by block (64 columns,
+// T of each block merged from its two panels' factors, which are built by
+// recursive doubling from the w vectors the panel kernel saves).
 #include <algorithm>
 
 #include "internal.h"
