@@ -146,6 +146,17 @@ int mps_swap(mps_t h, int site, int chi_max);
  * gate is applied on (hi-1, hi), and the SWAPs are undone in reverse order. */
 int mps_apply_2q_routed(mps_t h, int q1, int q2, const mps_c128 g[16], int chi_max);
 
+/* Site permutation by nearest-neighbour SWAPs in bubble-sort order (Sec. III-C,
+ * "Site permutation"; the re-embedding between horizontal and vertical nearest
+ * neighbours of Sec. III-D.2).  order[p] (a permutation of 0..n-1) is the current
+ * position of the site that must end at position p.  Each pass walks the chain
+ * left to right and applies mps_swap(p, chi_max) where the target positions of
+ * sites p and p+1 are out of order, until none is: the number of SWAPs is the
+ * number of inversions of the permutation, written to *swaps when swaps != NULL.
+ * Every SWAP truncates like a gate.  Host-side validation (MPS_E_ARG for a bad
+ * order) happens before any SWAP; asynchronous otherwise. */
+int mps_permute(mps_t h, const int* order, int chi_max, long long* swaps);
+
 /* All two-qubit gates of one circuit layer, on pairwise disjoint bonds
  * sites[j], sites[j]+1 (gates[16*j .. 16*j+15]) (the gates of a brick-wall
  * layer, Sec. III-D; network parallelism, Sec. I).  Requires MPS_POLICY_LOCAL

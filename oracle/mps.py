@@ -153,6 +153,31 @@ class OracleMPS:
         for b in range(q2 - 2, q1 - 1, -1):
             self.swap(b, chi_max)
 
+    def permute(self, order, chi_max=None):
+        """Site permutation by nearest-neighbour SWAPs, bubble-sort order (Sec. III-C,
+        "Site permutation"; the RCS re-embedding of Sec. III-D.2): afterwards chain
+        position p holds the site that was at position order[p].  Each pass walks the
+        chain left to right and swaps neighbours whose target positions are out of
+        order, updating the tuple of target positions as it goes.  Returns the
+        number of SWAPs (the number of inversions of the permutation)."""
+        n = len(self.sites)
+        order = [int(x) for x in order]
+        assert sorted(order) == list(range(n)), "order must be a permutation of the positions"
+        dest = [0] * n  # dest[q] = final position of the site now at q
+        for p, q in enumerate(order):
+            dest[q] = p
+        swaps = 0
+        changed = True
+        while changed:
+            changed = False
+            for q in range(n - 1):
+                if dest[q] > dest[q + 1]:
+                    self.swap(q, chi_max)
+                    dest[q], dest[q + 1] = dest[q + 1], dest[q]
+                    swaps += 1
+                    changed = True
+        return swaps
+
     def run(self, ops, chi_max=None):
         for op in ops:
             if op[0] == "1q":

@@ -74,6 +74,7 @@ SIGNATURES = {
     "mps_swap": (_I, [_P, _I, _I]),
     "mps_apply_2q_routed": (_I, [_P, _I, _I, ctypes.POINTER(mps_c128), _I]),
     "mps_apply_layer": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(mps_c128), _I, _I]),
+    "mps_permute": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_longlong)]),
     "mps_amplitude": (_I, [_P, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(mps_c128)]),
     "mps_fidelity_estimate": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
     "mps_overlap": (_I, [_P, _P, ctypes.POINTER(mps_c128)]),

@@ -1202,6 +1202,34 @@ int mps_apply_2q_routed(mps_t h, int q1, int q2, const mps_c128 g[16], int chi_m
   return MPS_OK;
 }
 
+int mps_permute(mps_t h, const int* order, int chi_max, long long* swaps) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!order) return fail(h, MPS_E_ARG, "permute: null order");
+  if (chi_max > h->chi_max) return fail(h, MPS_E_ARG, "permute: chi_max above the handle's");
+  std::vector<int> dest(h->n, -1);  // dest[q] = final position of the site now at q
+  for (int p = 0; p < h->n; ++p) {
+    const int q = order[p];
+    if (q < 0 || q >= h->n || dest[q] >= 0) return fail(h, MPS_E_ARG, "permute: order is not a permutation");
+    dest[q] = p;
+  }
+  long long count = 0;
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int q = 0; q + 1 < h->n; ++q) {
+      if (dest[q] > dest[q + 1]) {
+        rc = mps_swap(h, q, chi_max);
+        if (rc) return rc;
+        std::swap(dest[q], dest[q + 1]);
+        ++count;
+        changed = true;
+      }
+    }
+  }
+  if (swaps) *swaps = count;
+  return MPS_OK;
+}
+
 int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count, int chi_max) {
   int rc = usable(h);
   if (rc) return rc;

@@ -103,6 +103,14 @@ class MPS:
         g = _gate(np.concatenate([np.asarray(x).reshape(-1) for x in gates]) if cnt else np.zeros(16), 16 * max(cnt, 1))
         self._check(self.lib.mps_apply_layer(self.h, s, g, cnt, chi_max))
 
+    def permute(self, order, chi_max=0):
+        """Site permutation by bubble-sorted SWAPs: position p ends up holding the site
+        now at order[p].  Returns the number of SWAPs."""
+        o = (ctypes.c_int * max(len(order), 1))(*[int(x) for x in order])
+        cnt = ctypes.c_longlong()
+        self._check(self.lib.mps_permute(self.h, o, chi_max, ctypes.byref(cnt)))
+        return cnt.value
+
     def run(self, ops, chi_max=0):
         for op in ops:
             if op[0] == "1q":

@@ -299,6 +299,26 @@ def test_apply_layer_uneven_bonds_matches_one_by_one():
             assert np.array_equal(a.get_site(i, fmt="c64"), b.get_site(i, fmt="c64")), i
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+def test_permute_matches_oracle(prec, tol):
+    """Site permutation by bubble-sorted SWAPs with truncation (chi = 8 on 9 qubits):
+    same SWAP count as the oracle and the same state (Haar gates: no norm ties)."""
+    n, chi = 9, 8
+    ops = circuits.brickwall(n, 5, seed=17)
+    order = list(np.random.default_rng(8).permutation(n))
+    o = omps.OracleMPS(n, chi, "canon")
+    o.run(ops)
+    ns_o = o.permute(order)
+    with gpu_mps(n, chi, precision=prec) as m:
+        m.run(ops)
+        ns = m.permute(order)
+        assert ns == ns_o
+        assert m.fidelity() == pytest.approx(o.norm2(), rel=1e-9 if prec == "fp64" else 1e-5)
+        assert np.abs(sites_statevector(m) - o.statevector()).max() < tol
+        with pytest.raises(Exception):
+            m.permute([0] * n)
+
+
 def test_overlap_and_cross_precision():
     n = 10
     ops = circuits.brickwall(n, 6, seed=12)

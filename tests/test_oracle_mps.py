@@ -227,3 +227,34 @@ def test_random_canonical_state_has_unit_norm():
     m.set_sites(sites, centre=4)
     assert m.norm2() == pytest.approx(1.0, abs=1e-12)
     assert m.centre_norm2() == pytest.approx(1.0, abs=1e-12)
+
+
+def test_permute_is_qubit_transposition_without_truncation():
+    """Site permutation (bubble sort of SWAPs) without truncation: the state equals the
+    statevector with its qubit axes transposed accordingly, and the SWAP count is the
+    number of inversions of the permutation (brute force)."""
+    n = 6
+    rng = np.random.default_rng(41)
+    ops = circuits.brickwall(n, 4, seed=5)
+    m = omps.OracleMPS(n, 64, "canon")
+    m.run(ops)
+    v = m.statevector().reshape([2] * n)
+    order = list(rng.permutation(n))
+    swaps = m.permute(order)
+    inversions = sum(1 for a in range(n) for b in range(a + 1, n) if order[a] > order[b])
+    assert swaps == inversions
+    # position p now holds the qubit that was at position order[p]
+    w = np.transpose(v, order).reshape(-1)
+    assert np.abs(m.statevector() - w).max() < 1e-12
+
+
+def test_permute_identity_and_reversal():
+    n = 5
+    m = omps.OracleMPS(n, 32, "local")
+    m.run(circuits.brickwall(n, 3, seed=2))
+    v = m.statevector()
+    assert m.permute(list(range(n))) == 0
+    assert np.abs(m.statevector() - v).max() < 1e-14
+    assert m.permute(list(range(n - 1, -1, -1))) == n * (n - 1) // 2
+    w = np.transpose(v.reshape([2] * n), list(range(n - 1, -1, -1))).reshape(-1)
+    assert np.abs(m.statevector() - w).max() < 1e-12
