@@ -17,7 +17,10 @@ it.  Every step follows the paper's description:
   pivoting) stopped after k = min(2 chi_l, 2 chi_r, chi_max) pivots:
   the left site becomes Q[:, :k] reshaped (chi_l, 2, k) and the right site
   R[:k, :] P^T reshaped (k, 2, chi_r).  The state is never renormalised, so
-  its squared norm is the norm fidelity of Sec. III-E.
+  its squared norm is the norm fidelity of Sec. III-E.  With truncation="svd"
+  the split is the truncated SVD instead (Sec. III-B.2 Table III, compared with
+  pivoted QR in Sec. IV-A.1; oracle/svd.py): left site U[:, :k], right site
+  diag(S[:k]) V^dagger[:k, :], same k.
 * SWAP (Sec. III-C.4): the two-qubit path with the SWAP gate; a gate on
   non-adjacent positions lo < hi moves the qubit at lo rightwards by SWAPs on
   bonds (lo, lo+1) ... (hi-2, hi-1), applies the gate on (hi-1, hi), then
@@ -36,6 +39,7 @@ it.  Every step follows the paper's description:
 import numpy as np
 
 from . import qr as _qr
+from . import svd as _svd
 
 
 def _swap_gate():
@@ -50,11 +54,13 @@ SWAP = _swap_gate()
 
 
 class OracleMPS:
-    def __init__(self, n, chi_max, policy="canon"):
+    def __init__(self, n, chi_max, policy="canon", truncation="qrcp"):
         assert n >= 1 and chi_max >= 1 and policy in ("canon", "local")
+        assert truncation in ("qrcp", "svd")
         self.n = n
         self.chi_max = chi_max
         self.policy = policy
+        self.truncation = truncation
         self.sites = []
         for _ in range(n):
             s = np.zeros((1, 2, 1), dtype=np.complex128)
@@ -76,7 +82,7 @@ class OracleMPS:
         self.centre = centre
 
     def copy(self):
-        o = OracleMPS(self.n, self.chi_max, self.policy)
+        o = OracleMPS(self.n, self.chi_max, self.policy, self.truncation)
         o.sites = [s.copy() for s in self.sites]
         o.centre = self.centre
         o.discarded = list(self.discarded)
@@ -125,10 +131,14 @@ class OracleMPS:
         cl, cm, cr = a.shape[0], a.shape[2], b.shape[2]
         x = (a.reshape(2 * cl, cm) @ b.reshape(cm, 2 * cr)).reshape(cl, 2, 2, cr)
         theta = np.einsum("abcd,lcdr->labr", g, x).reshape(2 * cl, 2 * cr)
-        q, r, jpvt, disc = _qr.cpqr(theta, kmax=chi, pivot=True)
-        k = q.shape[1]
-        right = np.zeros((k, 2 * cr), dtype=np.complex128)
-        right[:, jpvt] = r
+        if self.truncation == "svd":
+            q, right, _, disc = _svd.svd_split(theta, chi)
+            k = q.shape[1]
+        else:
+            q, r, jpvt, disc = _qr.cpqr(theta, kmax=chi, pivot=True)
+            k = q.shape[1]
+            right = np.zeros((k, 2 * cr), dtype=np.complex128)
+            right[:, jpvt] = r
         self.sites[i] = np.ascontiguousarray(q).reshape(cl, 2, k)
         self.sites[i + 1] = right.reshape(k, 2, cr)
         if self.policy == "canon":

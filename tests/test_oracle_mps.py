@@ -202,7 +202,7 @@ def test_canonical_form_after_moves():
 
 
 def test_norm_fidelity_tracks_overlap_fidelity():
-    """Sec. III-E (Fig. 5): the norm fidelity approximates the overlap fidelity with
+    """Sec. III-E (norm-vs-overlap figure): the norm fidelity approximates the overlap fidelity with
     the exact state, and pivoted QR tends to underestimate it.  The overlap is
     taken with the truncated state normalised, |<E|T>|^2 / <T|T>."""
     n = 12
