@@ -535,6 +535,74 @@ def circuit_workload(args):
                       "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o}}), flush=True)
 
 
+def truncation_workload(args):
+    """Pivoted QR versus SVD bond truncation (Sec. IV-A.1) and norm versus overlap
+    fidelity (Sec. III-E), FP64, canonical policy.  (1) An n-qubit brick-wall circuit
+    run exactly (chi_max = 2^(n/2)) and truncated at several chi_max with each split:
+    CUDA-synchronised wall time, norm fidelity F_bar, overlap fidelity
+    F = |<exact|trunc>|^2 / (<exact|exact> <trunc|trunc>) from the GPU transfer-matrix
+    overlap, and r = F_bar - F.  (2) One apply on a saturated bond (chi_l = chi_m =
+    chi_r) with each split, mixed and FP64: seconds per apply and discarded weight."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from workloads import circuits, gates, states
+
+    __graft_entry__.build()
+    from paper_2505_06119_gb300 import MPS
+
+    n, depth = args.trunc_n, args.trunc_depth
+    ops = circuits.brickwall(n, depth, seed=7)
+    n2q = circuits.count_two_qubit(ops)
+    exact = MPS(n, 2 ** (n // 2), precision="fp64", policy="canon")
+    exact.run(ops)
+    fe = exact.fidelity()
+    rows = []
+    for chi in (int(x) for x in args.trunc_chi.split(",")):
+        for tr in ("qrcp", "svd"):
+            with MPS(n, chi, precision="fp64", policy="canon", truncation=tr) as m:
+                m.sync()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                m.run(ops)
+                m.sync()
+                dt = time.perf_counter() - t
+                fbar = m.fidelity()
+                f = abs(exact.overlap(m)) ** 2 / (fe * fbar)
+                rows.append({"chi_max": chi, "split": tr, "seconds": dt, "two_qubit_gates_per_s": n2q / dt,
+                             "norm_fidelity": fbar, "overlap_fidelity": f, "r": fbar - f})
+    exact.close()
+    gate_rows = []
+    for chi in (int(x) for x in args.svd_gate_chi.split(",")):
+        e = int(np.ceil(np.log2(chi))) + 1
+        nn, i = 2 * e + 2, e
+        g = gates.haar_unitary(np.random.default_rng(1234), 4)
+        for prec in ("mixed", "fp64"):
+            a, b = states.saturated_two_site(chi, chi, chi, seed=1234)
+            for tr in ("qrcp", "svd"):
+                with MPS(nn, chi, precision=prec, policy="local", truncation=tr) as m:
+                    m.set_site(i, a)
+                    m.set_site(i + 1, b)
+                    m.apply_2q(i, g)  # warm-up (and the first kernel loads)
+                    m.set_site(i, a)
+                    m.set_site(i + 1, b)
+                    d0 = m.discarded()[0]
+                    m.sync()
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    m.apply_2q(i, g)
+                    m.sync()
+                    dt = time.perf_counter() - t
+                    gate_rows.append({"chi": chi, "precision": prec, "split": tr, "seconds": dt,
+                                      "discarded": m.discarded()[0] - d0})
+    print(json.dumps({"workload": "truncation",
+                      "circuit": "%d-qubit chain, depth-%d brick-wall of Haar SU(4) + SU(2), seed 7" % (n, depth),
+                      "two_qubit_gates": n2q, "exact_norm": fe, "circuit_rows": rows,
+                      "gate": "one apply on a saturated bond chi_l = chi_m = chi_r, seed 1234, LOCAL policy",
+                      "gate_rows": gate_rows}), flush=True)
+
+
 def big_gate_workload(args):
     """One two-site apply at the paper's largest bond dimension (chi_l = chi_m = chi_r =
     args.big_chi, theta (2 chi)^2; the scope table's M5 timing), mixed path, through the
@@ -606,10 +674,15 @@ def main():
     ap.add_argument("--cpu-chi", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-overlap", action="store_true")
-    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit", "big"],
+    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit", "big", "truncation"],
                     help="gate: the headline metric; layer: batched vs one-by-one layer times; "
                          "circuit: whole-circuit throughput and fidelity deviation; "
-                         "big: one apply at a large bond dimension")
+                         "big: one apply at a large bond dimension; "
+                         "truncation: pivoted QR vs SVD splits (fidelity, runtime)")
+    ap.add_argument("--trunc-n", type=int, default=16)
+    ap.add_argument("--trunc-depth", type=int, default=16)
+    ap.add_argument("--trunc-chi", default="8,16,32")
+    ap.add_argument("--svd-gate-chi", default="64,256,512")
     ap.add_argument("--big-chi", type=int, default=16384)
     ap.add_argument("--layer-chi", default="256,1024,2048")
     ap.add_argument("--circuit", default="config2", choices=["config2", "grid"])
@@ -622,6 +695,8 @@ def main():
         circuit_workload(args)
     elif args.workload == "big":
         big_gate_workload(args)
+    elif args.workload == "truncation":
+        truncation_workload(args)
     elif args.impl == "reference":
         reference(args)
     else:

@@ -15,6 +15,9 @@
  *   3. stores Q[:, :k] as the new A_i (chi_l x 2 x k) and R[:k, :] P^T as the
  *      new A_{i+1} (k x 2 x chi_r).  The state is not renormalised: its squared
  *      norm is the norm fidelity F = <psi|psi> of Sec. III-E.
+ *   A handle created with truncation = MPS_TRUNC_SVD splits theta by its SVD
+ *   theta = U S V^dagger instead (the same table's SVD row, compared with
+ *   pivoted QR in Sec. IV-A.1): A_i = U[:, :k], A_{i+1} = diag(S[:k]) V^dagger[:k, :].
  *
  * Conventions
  *   - Site layout: row-major (chi_l, 2, chi_r), the flat row-major layout of
@@ -72,6 +75,14 @@ extern "C" {
 #define MPS_POLICY_CANON 0
 #define MPS_POLICY_LOCAL 1
 
+/* mps_config.truncation: how a two-site block is split and truncated */
+#define MPS_TRUNC_QRCP 0 /* truncated column-pivoted Householder QR (default; Sec. III-B.2) */
+#define MPS_TRUNC_SVD 1  /* truncated SVD by one-sided Jacobi (Sec. III-B.2 Table III, Sec. IV-A.1):
+                            the k largest singular values are kept, so the discarded weight is the
+                            least any rank-k split can reach.  Needs 2 (2 chi)^2 more elements of
+                            device memory, limits the handle to chi_max <= 4096, and is much slower
+                            than QRCP: every sweep of the Jacobi iteration touches all column pairs. */
+
 /* host element formats for mps_get_site / mps_set_site */
 #define MPS_HOST_C128 0
 #define MPS_HOST_C64 1
@@ -112,7 +123,8 @@ typedef struct {
   int debug_max_ctas;     /* testing only, normally 0: caps the CTAs of the cooperative QR
                              panel kernel so that small matrices take the paths of large
                              ones (more than 128 rows per CTA); negative: MPS_E_ARG */
-  int reserved[6];
+  int truncation;         /* MPS_TRUNC_QRCP (default) or MPS_TRUNC_SVD */
+  int reserved[5];
 } mps_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -132,7 +144,9 @@ int mps_destroy(mps_t h);
 int mps_apply_1q(mps_t h, int site, const mps_c128 u[4]);
 
 /* Two-qubit gate g on (site, site+1), split by truncated pivoted QR as in the
- * header comment (Sec. III-C.2, III-B.2).  chi_max (<= the handle's) caps the
+ * header comment (Sec. III-C.2, III-B.2), or by the truncated SVD when the handle
+ * was created with truncation = MPS_TRUNC_SVD (left site U[:, :k], right site
+ * diag(S[:k]) V^dagger[:k, :], same k).  chi_max (<= the handle's) caps the
  * new bond; chi_max <= 0 means the handle's value. */
 int mps_apply_2q(mps_t h, int site, const mps_c128 g[16], int chi_max);
 
@@ -225,7 +239,8 @@ const char* mps_last_error(mps_t h);
 #define MPS_KCLASS_SPLIT 5  /* site split / reshape / un-pivot */
 #define MPS_KCLASS_OTHER 6  /* 1q gates, conversions, observables */
 #define MPS_KCLASS_CANON 7  /* centre moves: plain QR / LQ, Q formation, absorption */
-#define MPS_KCLASS_COUNT 8
+#define MPS_KCLASS_SVD 8    /* SVD split: Jacobi sweeps, singular values, split (MPS_TRUNC_SVD) */
+#define MPS_KCLASS_COUNT 9
 
 typedef struct {
   long long launches;   /* kernel launches of this class since the last reset */

@@ -22,13 +22,15 @@ MPS_PREC_FP64 = 0
 MPS_PREC_MIXED = 1
 MPS_POLICY_CANON = 0
 MPS_POLICY_LOCAL = 1
+MPS_TRUNC_QRCP = 0
+MPS_TRUNC_SVD = 1
 MPS_HOST_C128 = 0
 MPS_HOST_C64 = 1
 MPS_FLAG_PROFILE = 1
 MPS_FLAG_TENSOR_CORES = 2
 MPS_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
-KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other", "canon"]
+KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other", "canon", "svd"]
 
 ERROR_NAMES = {0: "MPS_OK", -1: "MPS_E_ARG", -2: "MPS_E_NOMEM", -3: "MPS_E_CUDA",
                -4: "MPS_E_TIMEOUT", -5: "MPS_E_STATE", -6: "MPS_E_UNSUPPORTED"}
@@ -48,7 +50,7 @@ class mps_config(ctypes.Structure):
                 ("wait_timeout_s", ctypes.c_double), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("flags", ctypes.c_int),
                 ("debug_barrier_extra", ctypes.c_int), ("debug_max_ctas", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("truncation", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class mps_kstat(ctypes.Structure):
@@ -56,7 +58,7 @@ class mps_kstat(ctypes.Structure):
                 ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double)]
 
 
-KCLASS_COUNT = 8
+KCLASS_COUNT = 9
 
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p

@@ -28,6 +28,7 @@ constexpr int kMaxCoop = 1024;
 constexpr int kNormParts = 256;
 constexpr size_t kAlign = 256;
 constexpr int kDiscLog = 1 << 16;
+constexpr int kSvdMaxChi = 4096;  // MPS_TRUNC_SVD: theta at most 8192 x 8192
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -217,11 +218,9 @@ void gate_to_T(const mps_c128* g, int count, T* out) {
 // The two-site gate pipeline on raw device pointers (Sec. III-C.2):
 // theta contraction + gate -> truncated pivoted QR -> Q formation -> split.
 template <typename T>
-cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, int chi, const T* A, const T* B,
-                          const T* g, T* Aout, T* Bout, double* disc_slot, double* disc_total, cudaStream_t s,
-                          LaunchHooks* hk) {
+cudaError_t theta_step(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, const T* A, const T* B, const T* g,
+                       cudaStream_t s, LaunchHooks* hk) {
   const int m = 2 * cl, n = 2 * cr;
-  const int k = std::min(std::min(m, n), chi);
   hook_before(hk, MPS_KCLASS_THETA, ((double)m * cm + (double)cm * n + (double)m * n) * sizeof(T),
               8.0 * m * n * cm + 32.0 * m * n);
   if constexpr (std::is_same<T, c64>::value) {
@@ -233,6 +232,16 @@ cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int c
     CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s));
   }
   hook_after(hk, MPS_KCLASS_THETA, 1);
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, int chi, const T* A, const T* B,
+                          const T* g, T* Aout, T* Bout, double* disc_slot, double* disc_total, cudaStream_t s,
+                          LaunchHooks* hk) {
+  const int m = 2 * cl, n = 2 * cr;
+  const int k = std::min(std::min(m, n), chi);
+  CKE(theta_step<T>(w, kn, cl, cm, cr, A, B, g, s, hk));
   QrPlan<T> p = make_plan<T>(w, kn, m, n, k, 1, disc_slot, disc_total);
   CKE(qr_factor<T>(p, s, hk));
   CKE(qr_form_q<T>(p, w.Q, w.ldq, s, hk));
@@ -243,6 +252,65 @@ cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int c
   CKE(split_right<T>(w.W, w.ldw, w.jpvt, w.inv, k, n, Bout, s));
   hook_after(hk, MPS_KCLASS_SPLIT, 3);
   return cudaSuccess;
+}
+
+// scratch of the SVD split (MPS_TRUNC_SVD), carved from one buffer
+struct SvdLayout {
+  size_t X, V, sig2, tail, perm, rot, sweeps, part, fro2, total;
+};
+
+SvdLayout svd_layout(size_t esz, int mmax) {
+  SvdLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t mm = (size_t)std::max(mmax, 1);
+  L.X = take(esz * mm * mm);
+  L.V = take(esz * mm * mm);
+  L.sig2 = take(8 * mm);
+  L.tail = take(8 * mm);
+  L.perm = take(4 * mm);
+  L.rot = take(4 * (size_t)kSvdMaxSweeps);
+  L.sweeps = take(4);
+  L.part = take(8 * (size_t)kSvdParts);
+  L.fro2 = take(8);
+  L.total = off;
+  return L;
+}
+
+// The two-site gate with the truncated SVD split (MPS_TRUNC_SVD): theta as in
+// two_site_core, then svd_split instead of the pivoted QR.
+template <typename T>
+cudaError_t two_site_svd(const Ws<T>& w, char* sbase, const SvdLayout& SL, const Knobs& kn, int cl, int cm, int cr,
+                         int chi, const T* A, const T* B, const T* g, T* Aout, T* Bout, double* disc_slot,
+                         double* disc_total, cudaStream_t s, LaunchHooks* hk) {
+  const int m = 2 * cl, n = 2 * cr;
+  CKE(theta_step<T>(w, kn, cl, cm, cr, A, B, g, s, hk));
+  SvdPlan<T> p;
+  p.m = m;
+  p.n = n;
+  p.k = std::min(std::min(m, n), chi);
+  p.W = w.W;
+  p.ldw = w.ldw;
+  p.X = (T*)(sbase + SL.X);
+  p.V = (T*)(sbase + SL.V);
+  p.sig2 = (double*)(sbase + SL.sig2);
+  p.tail = (double*)(sbase + SL.tail);
+  p.perm = (int*)(sbase + SL.perm);
+  p.rot = (int*)(sbase + SL.rot);
+  p.sweeps = (int*)(sbase + SL.sweeps);
+  p.part = (double*)(sbase + SL.part);
+  p.fro2 = (double*)(sbase + SL.fro2);
+  p.bar = w.bar;
+  p.err = w.err;
+  p.timeout_ns = kn.timeout_ns;
+  p.barrier_extra = kn.barrier_extra;
+  p.discarded = disc_slot;
+  p.disc_total = disc_total;
+  return svd_split<T>(p, Aout, Bout, s, hk);
 }
 
 // ---------------------------------------------------------------------------
@@ -340,6 +408,10 @@ struct mps_s {
   WsLayout L;
   int64_t ldw = 0, ldq = 0;
   Knobs kn;
+  // SVD split scratch (MPS_TRUNC_SVD only)
+  int trunc = MPS_TRUNC_QRCP;
+  char* svd_ws = nullptr;
+  SvdLayout SL;
   // FP64 observables scratch
   double* d_partial = nullptr;
   double* d_scalar = nullptr;  // [0] norm, [1] total discarded
@@ -572,9 +644,13 @@ int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
   const int cl = h->bond[i], cm = h->bond[i + 1], cr = h->bond[i + 2];
   const int k = std::min(std::min(2 * cl, 2 * cr), chi);
   double* slot = h->d_disclog + (h->nsplit % kDiscLog);
-  cudaError_t e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
-                                   (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream,
-                                   &h->prof.hooks);
+  cudaError_t e;
+  if (h->trunc == MPS_TRUNC_SVD)
+    e = two_site_svd<T>(w, h->svd_ws, h->SL, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1],
+                        gt, (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
+  else
+    e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
+                         (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
   if (e != cudaSuccess) return cuda_fail(h, e, "apply_2q");
   h->bond[i + 1] = k;
   h->nsplit++;
@@ -623,7 +699,8 @@ int lanes_ready(mps_t h) {
 
 template <typename T>
 int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi) {
-  if (h->prof.enabled || count <= 1) {  // per-class event timing needs one stream
+  // per-class event timing needs one stream; the SVD split has one scratch per handle
+  if (h->prof.enabled || count <= 1 || h->trunc == MPS_TRUNC_SVD) {
     for (int j = 0; j < count; ++j) {
       int rc = apply_2q_t<T>(h, sites[j], gates + 16 * j, chi);
       if (rc) return rc;
@@ -990,12 +1067,15 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   if ((cfg.alloc == nullptr) != (cfg.free == nullptr)) return MPS_E_ARG;
   if (cfg.wait_timeout_s < 0) return MPS_E_ARG;
   if (cfg.debug_barrier_extra < 0 || cfg.debug_max_ctas < 0) return MPS_E_ARG;
+  if (cfg.truncation != MPS_TRUNC_QRCP && cfg.truncation != MPS_TRUNC_SVD) return MPS_E_ARG;
+  if (cfg.truncation == MPS_TRUNC_SVD && chi_max > kSvdMaxChi) return MPS_E_UNSUPPORTED;
   mps_s* h = new (std::nothrow) mps_s();
   if (!h) return MPS_E_NOMEM;
   h->n = n;
   h->chi_max = chi_max;
   h->prec = cfg.precision;
   h->policy = cfg.policy;
+  h->trunc = cfg.truncation;
   h->device = cfg.device;
   h->ualloc = cfg.alloc;
   h->ufree = cfg.free;
@@ -1065,7 +1145,11 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   h->d_partial = (double*)dev_alloc(h, sizeof(double) * (kNormParts + 8));
   h->d_disclog = (double*)dev_alloc(h, sizeof(double) * kDiscLog);
   h->d_vec = (c128*)dev_alloc(h, sizeof(c128) * (2 * (size_t)chicap + 2));
-  if (!h->ws || !h->d_partial || !h->d_disclog || !h->d_vec) {
+  if (h->trunc == MPS_TRUNC_SVD) {
+    h->SL = svd_layout(h->esz, 2 * chicap);
+    h->svd_ws = (char*)dev_alloc(h, h->SL.total);
+  }
+  if (!h->ws || !h->d_partial || !h->d_disclog || !h->d_vec || (h->trunc == MPS_TRUNC_SVD && !h->svd_ws)) {
     release(h);
     delete h;
     return MPS_E_NOMEM;

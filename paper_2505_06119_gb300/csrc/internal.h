@@ -179,4 +179,35 @@ inline void hook_after(LaunchHooks* h, int kclass, int nlaunch) {
   if (h && h->after) h->after(h, kclass, nlaunch);
 }
 
+// ---------------------------------------------------------------------------
+// Truncated SVD split by one-sided Jacobi (svd.cu; Sec. III-B.2 Table III).
+constexpr int kSvdMaxSweeps = 40;
+constexpr int kSvdParts = 256;
+
+template <typename T>
+struct SvdPlan {
+  int m, n, k;        // theta m x n, k kept singular values (k <= min(m, n))
+  const T* W;         // theta, column-major, ldw
+  int64_t ldw;
+  T* X;               // n * m scratch: theta^H, rotated in place
+  T* V;               // m * m scratch: accumulated rotations
+  double* sig2;       // m
+  double* tail;       // m
+  int* perm;          // m
+  int* rot;           // kSvdMaxSweeps
+  int* sweeps;        // 1: sweeps run (kSvdMaxSweeps + 1 = stopped unconverged)
+  double* part;       // kSvdParts
+  double* fro2;       // 1
+  unsigned* bar;      // grid barrier words (shared with the QR panels; stream-ordered)
+  int* err;           // device error word
+  unsigned long long timeout_ns;
+  unsigned barrier_extra;
+  double* discarded;  // out: sum of the discarded squared singular values
+  double* disc_total; // optional: discarded is also added here
+};
+
+// left site (row-major m x k) = V[:, kept]; right site (row-major k x n) = (theta^H V)[:, kept]^H
+template <typename T>
+cudaError_t svd_split(const SvdPlan<T>& p, T* Aout, T* Bout, cudaStream_t s, LaunchHooks* hooks);
+
 }  // namespace mpsg

@@ -29,7 +29,8 @@ def _gate(g, n):
 
 
 def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile=False,
-           wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False, debug_max_ctas=0):
+           wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False, debug_max_ctas=0,
+           truncation="qrcp"):
     lib = L.load()
     cfg = L.mps_config()
     lib.mps_config_init(ctypes.byref(cfg))
@@ -42,6 +43,7 @@ def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile
     cfg.device = device
     cfg.debug_barrier_extra = debug_barrier_extra
     cfg.debug_max_ctas = debug_max_ctas
+    cfg.truncation = {"qrcp": L.MPS_TRUNC_QRCP, "svd": L.MPS_TRUNC_SVD}[truncation]
     return cfg
 
 

@@ -68,6 +68,12 @@ def test_host_argument_checks(lib):
     lib.mps_config_init(ctypes.byref(cfg))
     cfg.debug_barrier_extra = -1
     assert lib.mps_create_ex(ctypes.byref(h), 4, 4, ctypes.byref(cfg)) == L.MPS_E_ARG
+    lib.mps_config_init(ctypes.byref(cfg))
+    assert cfg.truncation == L.MPS_TRUNC_QRCP
+    cfg.truncation = 2
+    assert lib.mps_create_ex(ctypes.byref(h), 4, 4, ctypes.byref(cfg)) == L.MPS_E_ARG
+    cfg.truncation = L.MPS_TRUNC_SVD  # the SVD split is limited to chi_max <= 4096
+    assert lib.mps_create_ex(ctypes.byref(h), 30, 8192, ctypes.byref(cfg)) == L.MPS_E_UNSUPPORTED
     assert lib.mps_destroy(None) == L.MPS_OK
     assert lib.mps_apply_2q(None, 0, None, 4) == L.MPS_E_ARG
     assert lib.mps_version() >= 100
