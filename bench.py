@@ -555,11 +555,13 @@ def truncation_workload(args):
     n, depth = args.trunc_n, args.trunc_depth
     ops = circuits.brickwall(n, depth, seed=7)
     n2q = circuits.count_two_qubit(ops)
+    chis = [int(x) for x in args.trunc_chi.split(",") if x]
     exact = MPS(n, 2 ** (n // 2), precision="fp64", policy="canon")
-    exact.run(ops)
+    if chis:
+        exact.run(ops)
     fe = exact.fidelity()
     rows = []
-    for chi in (int(x) for x in args.trunc_chi.split(",")):
+    for chi in chis:
         for tr in ("qrcp", "svd"):
             with MPS(n, chi, precision="fp64", policy="canon", truncation=tr) as m:
                 m.sync()
@@ -574,7 +576,7 @@ def truncation_workload(args):
                              "norm_fidelity": fbar, "overlap_fidelity": f, "r": fbar - f})
     exact.close()
     gate_rows = []
-    for chi in (int(x) for x in args.svd_gate_chi.split(",")):
+    for chi in (int(x) for x in args.svd_gate_chi.split(",") if x):
         e = int(np.ceil(np.log2(chi))) + 1
         nn, i = 2 * e + 2, e
         g = gates.haar_unitary(np.random.default_rng(1234), 4)

@@ -82,19 +82,34 @@ __device__ __forceinline__ void round_pair(int r, int j, int Mp, int& p, int& q)
   q = max(a, b);
 }
 
-// x <- c x - s1 y,  y <- s2 x + c y  over `len` elements, one warp
+// x <- c x - s1 y,  y <- s2 x + c y  over `len` elements, one warp; kChunk
+// elements per lane are loaded before any is used, so their latencies overlap
 template <typename T, typename R>
 __device__ __forceinline__ void rotate_cols(T* __restrict__ xp, T* __restrict__ xq, int len, R c, T s1, T s2,
                                             int lane) {
-  for (int t = lane; t < len; t += 32) {
-    const T x = xp[t], y = xq[t];
-    T xn, yn;
-    xn.re = c * x.re - (s1.re * y.re - s1.im * y.im);
-    xn.im = c * x.im - (s1.re * y.im + s1.im * y.re);
-    yn.re = (s2.re * x.re - s2.im * x.im) + c * y.re;
-    yn.im = (s2.re * x.im + s2.im * x.re) + c * y.im;
-    xp[t] = xn;
-    xq[t] = yn;
+  for (int t0 = 0; t0 < len; t0 += 32 * kChunk) {
+    T x[kChunk], y[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int t = t0 + u * 32 + lane;
+      if (t < len) {
+        x[u] = xp[t];
+        y[u] = xq[t];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int t = t0 + u * 32 + lane;
+      if (t < len) {
+        T xn, yn;
+        xn.re = c * x[u].re - (s1.re * y[u].re - s1.im * y[u].im);
+        xn.im = c * x[u].im - (s1.re * y[u].im + s1.im * y[u].re);
+        yn.re = (s2.re * x[u].re - s2.im * x[u].im) + c * y[u].re;
+        yn.im = (s2.re * x[u].im + s2.im * x[u].re) + c * y[u].im;
+        xp[t] = xn;
+        xq[t] = yn;
+      }
+    }
   }
 }
 
