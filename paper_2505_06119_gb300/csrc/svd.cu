@@ -30,16 +30,24 @@
 // butterfly whose result is the same in every lane), so runs are reproducible
 // and every lane derives the same rotation.
 //
-// Precision: the data (X, V) and the rotations stay in the handle's precision;
-// the pair sums, the rotation parameters and the squared norms are FP64.
+// Precision: the data (X, V), the pair sums and the rotation parameters are in
+// the handle's precision; in complex64 the rotation (cs, sn e^{i phi}) is scaled
+// to unit norm in FP64 before it is rounded, which keeps the accumulated V
+// orthonormal to FP32 rounding (without it the FP32 parameter chain leaves
+// rotations off unitary by several ulps and V drifts ten times further).  The
+// squared singular values, their order and the discarded weight are FP64.
+//
+// Grid: one warp per pair; warps per CTA are chosen so that the m/2 pairs of a
+// round spread over all SMs (the FP64 work of a pair competes for the few FP64
+// units of an SM sub-partition).  The two V columns of a pair are prefetched
+// into L1 while the pair sums are formed, so their rotation does not wait on L2.
 #include "internal.h"
 
 namespace mpsg {
 
 namespace {
 
-constexpr int kJW = 8;  // warps (pairs in flight) per CTA
-constexpr int kJT = 32 * kJW;
+constexpr int kJMaxWarps = 8;  // warps (pairs in flight) per CTA, at most
 constexpr int kChunk = 8;  // elements per lane summed in the data precision before FP64
 
 template <typename T>
@@ -113,13 +121,35 @@ __device__ __forceinline__ void rotate_cols(T* __restrict__ xp, T* __restrict__ 
   }
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* ptr) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
+}
+
+// lanes prefetch the 128-byte lines of one column of `len` elements
+template <typename T>
+__device__ __forceinline__ void prefetch_col(const T* col, int len, int lane) {
+  constexpr int per_line = 128 / (int)sizeof(T);
+  for (int t = lane * per_line; t < len; t += 32 * per_line) prefetch_l1(col + t);
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // one pair (p < q) by one warp; returns 1 if it rotated
 template <typename T>
-__device__ int jacobi_pair(const JacobiArgs<T>& a, int p, int q, int lane, double zero_level) {
+__device__ int jacobi_pair(const JacobiArgs<T>& a, int p, int q, int lane, typename real_of<T>::type zero_level) {
   using R = typename real_of<T>::type;
   T* xp = a.X + (int64_t)p * a.ldx;
   T* xq = a.X + (int64_t)q * a.ldx;
-  double saa = 0.0, sbb = 0.0, scr = 0.0, sci = 0.0;
+  T* vp = a.V + (int64_t)p * a.ldv;
+  T* vq = a.V + (int64_t)q * a.ldv;
+  prefetch_col(vp, a.M, lane);
+  prefetch_col(vq, a.M, lane);
+  R saa = 0, sbb = 0, scr = 0, sci = 0;
   for (int t0 = 0; t0 < a.len; t0 += 32 * kChunk) {
     R caa = 0, cbb = 0, ccr = 0, cci = 0;
 #pragma unroll
@@ -133,43 +163,51 @@ __device__ int jacobi_pair(const JacobiArgs<T>& a, int p, int q, int lane, doubl
         cci = fma(x.re, y.im, fma(-x.im, y.re, cci));   // Im conj(x) y
       }
     }
-    saa += (double)caa;
-    sbb += (double)cbb;
-    scr += (double)ccr;
-    sci += (double)cci;
+    saa += caa;
+    sbb += cbb;
+    scr += ccr;
+    sci += cci;
   }
-  saa = warp_sum(saa);
-  sbb = warp_sum(sbb);
-  scr = warp_sum(scr);
-  sci = warp_sum(sci);
+  saa = warp_sum_r(saa);
+  sbb = warp_sum_r(sbb);
+  scr = warp_sum_r(scr);
+  sci = warp_sum_r(sci);
   if (!(saa > zero_level) || !(sbb > zero_level)) return 0;
-  const double ac = hypot(scr, sci);
-  if (!(ac > a.tol * sqrt(saa) * sqrt(sbb))) return 0;
-  const double zeta = (sbb - saa) / (2.0 * ac);
-  const double az = fabs(zeta);
-  const double t = az > 1e150 ? 0.5 / zeta : (zeta >= 0.0 ? 1.0 : -1.0) / (az + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-  const double er = scr / ac, ei = sci / ac;
-  const R c = (R)cs;
-  const T s1 = mk<R>((R)(sn * er), (R)(-sn * ei));  // sn e^{-i phi}
-  const T s2 = mk<R>((R)(sn * er), (R)(sn * ei));   // sn e^{+i phi}
-  rotate_cols<T, R>(xp, xq, a.len, c, s1, s2, lane);
-  rotate_cols<T, R>(a.V + (int64_t)p * a.ldv, a.V + (int64_t)q * a.ldv, a.M, c, s1, s2, lane);
+  const R ac = hypot(scr, sci);
+  if (!(ac > (R)a.tol * sqrt(saa) * sqrt(sbb))) return 0;
+  const R zeta = (sbb - saa) / (R(2) * ac);
+  const R az = fabs(zeta);
+  const R big = sizeof(R) == 4 ? R(1e15) : R(1e150);
+  const R t = az > big ? R(0.5) / zeta : (zeta >= R(0) ? R(1) : R(-1)) / (az + sqrt(R(1) + zeta * zeta));
+  R cs = R(1) / sqrt(R(1) + t * t);
+  R sr = cs * t * (scr / ac), si = cs * t * (sci / ac);  // sn e^{i phi}
+  if constexpr (sizeof(R) == 4) {
+    const double nn = (double)cs * cs + (double)sr * sr + (double)si * si;
+    const double sc = rsqrt(nn);
+    cs = (R)(cs * sc);
+    sr = (R)(sr * sc);
+    si = (R)(si * sc);
+  }
+  const T s1 = mk<R>(sr, -si);  // sn e^{-i phi}
+  const T s2 = mk<R>(sr, si);   // sn e^{+i phi}
+  rotate_cols<T, R>(xp, xq, a.len, cs, s1, s2, lane);
+  rotate_cols<T, R>(vp, vq, a.M, cs, s1, s2, lane);
   return 1;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kJT) jacobi_kernel(JacobiArgs<T> a) {
+__global__ void __launch_bounds__(32 * kJMaxWarps) jacobi_kernel(JacobiArgs<T> a) {
   using R = typename real_of<T>::type;
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * kJW + (threadIdx.x >> 5);
-  const int nw = gridDim.x * kJW;
+  const int wpc = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpc + (threadIdx.x >> 5);
+  const int nw = gridDim.x * wpc;
   const int Mp = a.M + (a.M & 1);
   const int P = Mp / 2;
   const unsigned expected = gridDim.x + a.barrier_extra;
   const double eps = sizeof(R) == 4 ? 1.1920928955078125e-07 : 2.220446049250313e-16;
   const double zl = eps * sqrt((double)a.len);
-  const double zero_level = zl * zl * (*a.fro2);
+  const R zero_level = (R)(zl * zl * (*a.fro2));
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     int rotated = 0;
     for (int r = 0; r < Mp - 1; ++r) {
@@ -291,20 +329,24 @@ __global__ void svd_right_kernel(const T* X, int64_t ldx, const int* perm, int M
   site[(int64_t)t * n + c] = cconj(X[c + (int64_t)j * ldx]);
 }
 
+// launch shape of the Jacobi kernel for `pairs` pairs per round: warps per CTA so
+// that the pairs spread over every SM, CTAs capped by co-residency
 template <typename T>
-int jacobi_grid(int pairs) {
-  static int cap[2] = {0, 0};
-  int& c = cap[sizeof(T) == 8 ? 0 : 1];
+void jacobi_shape(int pairs, int& G, int& warps) {
+  static int cap[2][kJMaxWarps + 1] = {};
+  const int sms = num_sms();
+  warps = std::max(1, std::min(kJMaxWarps, (pairs + sms - 1) / sms));
+  int& c = cap[sizeof(T) == 8 ? 0 : 1][warps];
   if (c == 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, kJT, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, 32 * warps, 0) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
     }
-    c = per_sm * num_sms();
+    c = per_sm * sms;
   }
-  return std::max(1, std::min(c, (pairs + kJW - 1) / kJW));
+  G = std::max(1, std::min(c, (pairs + warps - 1) / warps));
 }
 
 }  // namespace
@@ -336,9 +378,10 @@ cudaError_t svd_split(const SvdPlan<T>& p, T* Aout, T* Bout, cudaStream_t s, Lau
   a.barrier_extra = p.barrier_extra;
   a.tol = (sizeof(T) == 8 ? 1.1920928955078125e-07 : 2.220446049250313e-16) * sqrt((double)n);
   a.max_sweeps = kSvdMaxSweeps;
-  const int G = jacobi_grid<T>((m + 1) / 2);
+  int G = 1, warps = 1;
+  jacobi_shape<T>((m + 1) / 2, G, warps);
   void* args[] = {&a};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel<T>, dim3(G), dim3(kJT), args, 0, s);
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel<T>, dim3(G), dim3(32 * warps), args, 0, s);
   if (e != cudaSuccess) return e;
   col_norm2_kernel<T><<<(m + 7) / 8, 256, 0, s>>>(p.X, n, n, m, p.sig2, p.err);
   sv_rank_kernel<<<(m + 255) / 256, 256, 0, s>>>(p.sig2, m, k, p.perm, p.tail);
