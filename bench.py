@@ -535,6 +535,27 @@ def circuit_workload(args):
                       "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o}}), flush=True)
 
 
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # CUDA-core FFMA peak at the 2070 MHz maximum clock
+FP64_TFLOPS = 1.25  # nominal GB300 FP64 rate
+
+
+def svd_roofline(m, rows, cols, prec, seconds):
+    """Algorithmic work of the Jacobi iteration of the last SVD split: every sweep forms
+    the pair sums of all rows*(rows-1)/2 column pairs of theta^H (16 flop per element of
+    a column of length cols), and each applied rotation updates two columns of theta^H
+    and two of V (20 flop per element pair, lengths cols and rows).  The rate is taken
+    over the whole apply (theta and the split included), so it is a lower bound for the
+    Jacobi kernel, against the CUDA-core FP32 (mixed) or FP64 peak: the iteration runs on
+    the CUDA cores, not the tensor cores."""
+    sweeps, rots = m.svd_stats()
+    pairs = rows * (rows - 1) // 2
+    flops = min(sweeps, 40) * pairs * 16.0 * cols + rots * 20.0 * (cols + rows)
+    peak = FP32_ALU_TFLOPS if prec == "mixed" else FP64_TFLOPS
+    tf = flops / seconds / 1e12
+    return {"jacobi_sweeps": sweeps, "jacobi_rotations": rots, "jacobi_gflop": flops / 1e9,
+            "achieved_tflops": tf, "alu_peak_tflops": peak, "frac": tf / peak}
+
+
 def truncation_workload(args):
     """Pivoted QR versus SVD bond truncation (Sec. IV-A.1) and norm versus overlap
     fidelity (Sec. III-E), FP64, canonical policy.  (1) An n-qubit brick-wall circuit
@@ -596,8 +617,11 @@ def truncation_workload(args):
                     m.apply_2q(i, g)
                     m.sync()
                     dt = time.perf_counter() - t
-                    gate_rows.append({"chi": chi, "precision": prec, "split": tr, "seconds": dt,
-                                      "discarded": m.discarded()[0] - d0})
+                    row = {"chi": chi, "precision": prec, "split": tr, "seconds": dt,
+                           "discarded": m.discarded()[0] - d0}
+                    if tr == "svd":
+                        row.update(svd_roofline(m, 2 * chi, 2 * chi, prec, dt))
+                    gate_rows.append(row)
     print(json.dumps({"workload": "truncation",
                       "circuit": "%d-qubit chain, depth-%d brick-wall of Haar SU(4) + SU(2), seed 7" % (n, depth),
                       "two_qubit_gates": n2q, "exact_norm": fe, "circuit_rows": rows,

@@ -223,6 +223,13 @@ int mps_move_centre(mps_t h, int target);
  * two-site splits so far.  Synchronous. */
 int mps_discarded_weight(mps_t h, double* total, long long* count);
 
+/* Iteration record of the most recent SVD split (handles created with
+ * truncation = MPS_TRUNC_SVD): *sweeps = Jacobi sweeps run (the last one found
+ * every pair orthogonal; kSvdMaxSweeps + 1 = stopped at the sweep limit), and
+ * *rotations = plane rotations applied over all sweeps.  0 and 0 before the first
+ * split.  MPS_E_STATE on a QRCP handle.  Synchronous. */
+int mps_svd_last_stats(mps_t h, int* sweeps, long long* rotations);
+
 /* Use `stream` (a cudaStream_t) for all further work; NULL = the handle's own. */
 int mps_set_stream(mps_t h, void* stream);
 /* Wait for all queued work; surfaces device-side errors. */

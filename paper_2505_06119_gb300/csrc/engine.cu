@@ -1159,6 +1159,7 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->L.err, 0, 16, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_scalar, 0, 8 * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(sites, 0, total, h->stream);
+  if (e == cudaSuccess && h->svd_ws) e = cudaMemsetAsync(h->svd_ws + h->SL.rot, 0, h->SL.part - h->SL.rot, h->stream);
   // |0...0>: every site (1, 2, 1) = [1, 0]
   if (e == cudaSuccess) {
     std::vector<char> one(h->esz, 0);
@@ -1456,6 +1457,26 @@ int mps_discarded_weight(mps_t h, double* total, long long* count) {
   rc = check_device_error(h);
   if (rc) return rc;
   *count = h->nsplit;
+  return MPS_OK;
+}
+
+int mps_svd_last_stats(mps_t h, int* sweeps, long long* rotations) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!sweeps || !rotations) return fail(h, MPS_E_ARG, "svd_last_stats: null pointer");
+  if (h->trunc != MPS_TRUNC_SVD) return fail(h, MPS_E_STATE, "svd_last_stats: the handle splits by pivoted QR");
+  int sw = 0;
+  int rot[kSvdMaxSweeps];
+  CUTRY(h, cudaMemcpyAsync(&sw, h->svd_ws + h->SL.sweeps, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+        "svd_last_stats");
+  CUTRY(h, cudaMemcpyAsync(rot, h->svd_ws + h->SL.rot, sizeof(rot), cudaMemcpyDeviceToHost, h->stream),
+        "svd_last_stats");
+  rc = check_device_error(h);
+  if (rc) return rc;
+  long long tot = 0;
+  for (int j = 0; j < std::min(std::max(sw, 0), kSvdMaxSweeps); ++j) tot += rot[j];
+  *sweeps = sw;
+  *rotations = tot;
   return MPS_OK;
 }
 

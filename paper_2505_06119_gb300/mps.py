@@ -188,6 +188,13 @@ class MPS:
         self._check(self.lib.mps_discarded_weight(self.h, ctypes.byref(t), ctypes.byref(c)))
         return t.value, c.value
 
+    def svd_stats(self):
+        """(sweeps, rotations) of the most recent SVD split (truncation="svd" handles)."""
+        sw = ctypes.c_int()
+        rot = ctypes.c_longlong()
+        self._check(self.lib.mps_svd_last_stats(self.h, ctypes.byref(sw), ctypes.byref(rot)))
+        return sw.value, rot.value
+
     def sync(self):
         self._check(self.lib.mps_sync(self.h))
 

@@ -192,3 +192,24 @@ def test_svd_bounded_wait_expiry():
         m.sync()
     assert ei.value.code == L.MPS_E_TIMEOUT
     m.close()
+
+
+def test_svd_iteration_record():
+    """mps_svd_last_stats reports the sweeps and rotations of the last split; the
+    iteration converged (a final sweep without rotations) well inside the limit."""
+    from paper_2505_06119_gb300 import MPSError, _lib as L
+
+    rng = np.random.default_rng(3)
+    a = states.complex_gaussian(rng, (32, 2, 32))
+    b = states.complex_gaussian(rng, (32, 2, 32))
+    with gpu_mps(14, 32, precision="mixed", policy="local", truncation="svd") as m:
+        assert m.svd_stats() == (0, 0)
+        m.set_site(5, a)
+        m.set_site(6, b)
+        m.apply_2q(5, gates.haar_unitary(rng, 4))
+        sweeps, rots = m.svd_stats()
+        assert 2 <= sweeps <= 20 and rots >= 64 * 63 // 2
+    with gpu_mps(6, 8) as q:
+        with pytest.raises(MPSError) as ei:
+            q.svd_stats()
+        assert ei.value.code == L.MPS_E_STATE
