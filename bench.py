@@ -489,8 +489,12 @@ def circuit_workload(args):
     """Whole circuits (the scope table's M2 and, reduced, M3 workloads), mixed and FP64
     paths under the canonical policy: two-qubit gate applies per second of each path
     (CUDA-synchronised wall clock over the whole circuit, routed gates counted once) and
-    the mixed-vs-FP64 fidelity deviation at the end (R15: relative norm-fidelity
-    difference and 1 - |<mix|64>|^2 / (<mix|mix><64|64>), contractions in FP64)."""
+    the mixed-vs-FP64 fidelity deviation at the end (both readings of the deviation:
+    relative norm-fidelity difference and 1 - |<mix|64>|^2 / (<mix|mix><64|64>),
+    contractions in FP64).  Grid circuits also report the SWAP count, and with the
+    permutation approach (--circuit grid-perm) the norm fidelity before and after every
+    permutation layer and the average norm fidelity per swap
+    f_swap = (F_after / F_before)^(1 / swaps) of Sec. III-E (probe time excluded)."""
     import numpy as np
     import torch
 
@@ -507,22 +511,50 @@ def circuit_workload(args):
     else:
         rows, cols, cyc = (int(x) for x in args.grid.split("x"))
         n, chi = rows * cols, args.grid_chi
-        ops = circuits.grid_rcs(rows, cols, cyc, seed=11)
-        name = ("%dx%d grid random circuit snaked onto a chain, %d cycles ABCDCDAB, paper 1q gate set and "
-                "fSim, SWAP-routed vertical couplers, chi_max=%d, seed 11" % (rows, cols, cyc, chi))
+        if args.circuit == "grid":
+            ops = circuits.grid_rcs(rows, cols, cyc, seed=11)
+            how = "SWAP-routed vertical couplers (chains there and back)"
+        else:
+            ops = circuits.grid_rcs_permuted(rows, cols, cyc, seed=11)
+            how = ("vertical couplers in a column-snake embedding reached by bubble-sort site "
+                   "permutations between the A/B and C/D layers")
+        name = ("%dx%d grid random circuit, %d cycles ABCDCDAB, paper 1q gate set and fSim, %s, chi_max=%d, "
+                "seed 11" % (rows, cols, cyc, how, chi))
     n2q = circuits.count_two_qubit(ops)
+    swaps = sum(2 * (abs(op[2] - op[1]) - 1) for op in ops if op[0] == "2q") + \
+        sum(circuits.inversions(op[1]) for op in ops if op[0] == "perm")
     res = {}
     states_ = {}
     for prec in ("mixed", "fp64"):
         m = MPS(n, chi, precision=prec, policy="canon")
         m.sync()
         torch.cuda.synchronize()
+        layers = []
+        probe_s = 0.0
         t = time.perf_counter()
-        m.run(ops)
+        for op in ops:
+            if op[0] != "perm":
+                m.run([op])
+                continue
+            # norm fidelity before and after the permutation layer (Sec. III-E: f_swap)
+            t0 = time.perf_counter()
+            f0 = m.fidelity()
+            probe_s += time.perf_counter() - t0
+            nsw = m.permute(op[1])
+            t0 = time.perf_counter()
+            f1 = m.fidelity()
+            probe_s += time.perf_counter() - t0
+            layers.append({"swaps": nsw, "f_before": f0, "f_after": f1,
+                           "f_swap": (f1 / f0) ** (1.0 / nsw) if nsw else 1.0})
         m.sync()
-        dt = time.perf_counter() - t
+        dt = time.perf_counter() - t - probe_s
         res[prec] = {"seconds": dt, "two_qubit_gates_per_s": n2q / dt, "fidelity": m.fidelity(),
                      "max_bond": max(m.bond_dims())}
+        if layers:
+            tot_sw = sum(x["swaps"] for x in layers)
+            ratio = float(np.prod([x["f_after"] / x["f_before"] for x in layers]))
+            res[prec]["permutation_layers"] = layers
+            res[prec]["f_swap_average"] = ratio ** (1.0 / tot_sw)
         states_[prec] = m
     mm, m64 = states_["mixed"], states_["fp64"]
     o = mm.overlap(m64)
@@ -530,7 +562,7 @@ def circuit_workload(args):
     dev_f = abs(res["mixed"]["fidelity"] - res["fp64"]["fidelity"]) / res["fp64"]["fidelity"]
     for m in states_.values():
         m.close()
-    print(json.dumps({"workload": "circuit", "circuit": name, "two_qubit_gates": n2q, "paths": res,
+    print(json.dumps({"workload": "circuit", "circuit": name, "two_qubit_gates": n2q, "swaps": swaps, "paths": res,
                       "speedup_mixed_vs_fp64": res["fp64"]["seconds"] / res["mixed"]["seconds"],
                       "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o}}), flush=True)
 
@@ -711,7 +743,7 @@ def main():
     ap.add_argument("--svd-gate-chi", default="64,256,512")
     ap.add_argument("--big-chi", type=int, default=16384)
     ap.add_argument("--layer-chi", default="256,1024,2048")
-    ap.add_argument("--circuit", default="config2", choices=["config2", "grid"])
+    ap.add_argument("--circuit", default="config2", choices=["config2", "grid", "grid-perm"])
     ap.add_argument("--grid-chi", type=int, default=256)
     ap.add_argument("--grid", default="7x7x12", help="rows x cols x cycles of the grid circuit")
     args = ap.parse_args()

@@ -192,6 +192,8 @@ class OracleMPS:
         for op in ops:
             if op[0] == "1q":
                 self.apply_1q(op[1], op[2])
+            elif op[0] == "perm":
+                self.permute(op[1], chi_max)
             else:
                 self.apply_2q_routed(op[1], op[2], op[3], chi_max)
 

@@ -33,12 +33,19 @@ def apply_2q(v, n, q1, q2, g):
     return np.transpose(t, order).reshape(-1)
 
 
+def permute(v, n, order):
+    """Qubit permutation: axis p of the result is axis order[p] of v."""
+    return np.transpose(v.reshape([2] * n), list(order)).reshape(-1)
+
+
 def run(ops, n, v=None):
     if v is None:
         v = zero_state(n)
     for op in ops:
         if op[0] == "1q":
             v = apply_1q(v, n, op[1], op[2])
+        elif op[0] == "perm":
+            v = permute(v, n, op[1])
         else:
             v = apply_2q(v, n, op[1], op[2], op[3])
     return v

@@ -117,6 +117,8 @@ class MPS:
         for op in ops:
             if op[0] == "1q":
                 self.apply_1q(op[1], op[2])
+            elif op[0] == "perm":
+                self.permute(op[1], chi_max)
             elif abs(op[1] - op[2]) == 1 and op[1] < op[2]:
                 self.apply_2q(op[1], op[3], chi_max)
             else:

@@ -240,6 +240,24 @@ def test_routed_truncated_matches_oracle():
             assert abs(m.amplitude(bits) - ref.amplitude(bits)) < 1e-10
 
 
+def test_permuted_grid_truncated_matches_oracle():
+    """The permutation approach to the vertical couplers (Sec. III-D.2; row snake for
+    A/B, column snake for C/D, bubble-sort permutations in between) with truncation:
+    norm fidelity, amplitudes and the state against the oracle (Haar 1q gates)."""
+    ops = circuits.grid_rcs_permuted(3, 4, 8, seed=11, singles="haar")
+    ref = omps.OracleMPS(12, 8, "canon")
+    ref.run(ops)
+    with gpu_mps(12, 8, precision="fp64") as m:
+        m.run(ops)
+        assert m.bond_dims() == ref.bond_dims()
+        assert m.fidelity() == pytest.approx(ref.norm2(), rel=1e-9)
+        rng = np.random.default_rng(2)
+        for _ in range(32):
+            bits = rng.integers(0, 2, 12)
+            assert abs(m.amplitude(bits) - ref.amplitude(bits)) < 1e-10
+    assert ref.norm2() < 0.999
+
+
 def test_centre_moves_keep_state_and_canonical_form():
     n = 10
     ops = circuits.brickwall(n, 6, seed=4)

@@ -258,3 +258,41 @@ def test_permute_identity_and_reversal():
     assert m.permute(list(range(n - 1, -1, -1))) == n * (n - 1) // 2
     w = np.transpose(v.reshape([2] * n), list(range(n - 1, -1, -1))).reshape(-1)
     assert np.abs(m.statevector() - w).max() < 1e-12
+
+
+def test_permuted_grid_circuit_is_the_routed_circuit():
+    """The permutation approach to the vertical couplers (Sec. III-D.2): row-snake for
+    the horizontal patterns, column-snake for the vertical ones, a site permutation in
+    between and one back at the end.  Without truncation it prepares exactly the state
+    of the SWAP-routed circuit with the same gates."""
+    rows, cols, cyc = 3, 4, 8
+    routed = circuits.grid_rcs(rows, cols, cyc, seed=5)
+    permuted = circuits.grid_rcs_permuted(rows, cols, cyc, seed=5)
+    n = rows * cols
+    v = sv.run(routed, n)
+    assert np.abs(sv.run(permuted, n) - v).max() < 1e-12
+    perms = [op for op in permuted if op[0] == "perm"]
+    assert len(perms) == 2  # AB | CDCD | AB: to the column snake and back
+    for op in permuted:
+        if op[0] == "2q":
+            assert abs(op[1] - op[2]) == 1  # every coupler is a chain neighbour
+    m = omps.OracleMPS(n, 64, "canon")
+    m.run(permuted)
+    assert np.abs(m.statevector() - v).max() < 1e-12
+
+
+def test_embedding_change_swap_counts():
+    """2 x 2 grid by hand: row snake (00, 01, 11, 10) to column snake (00, 10, 11, 01)
+    is the permutation order = [0, 3, 2, 1], three inversions; the oracle's bubble sort
+    applies exactly the inversion count of each embedding change."""
+    row = lambda r, c: circuits.snake_position(r, c, 2)  # noqa: E731
+    col = lambda r, c: circuits.column_snake_position(r, c, 2)  # noqa: E731
+    assert circuits.embedding_change(2, 2, row, col) == [0, 3, 2, 1]
+    assert circuits.inversions([0, 3, 2, 1]) == 3
+    rows, cols = 3, 3
+    row = lambda r, c: circuits.snake_position(r, c, cols)  # noqa: E731
+    col = lambda r, c: circuits.column_snake_position(r, c, rows)  # noqa: E731
+    order = circuits.embedding_change(rows, cols, row, col)
+    m = omps.OracleMPS(rows * cols, 16, "canon")
+    m.run(circuits.brickwall(rows * cols, 3, seed=1))
+    assert m.permute(order) == circuits.inversions(order) == 15

@@ -6,6 +6,8 @@ A circuit is a list of operations:
 * ``("2q", q1, q2, g)``  two-qubit gate ``g`` (4x4, see ``gates``) on the
   ordered pair of positions (q1, q2).  The positions need not be adjacent; a
   consumer routes non-adjacent pairs with SWAP chains (Sec. III-C.4).
+* ``("perm", order)``    site permutation (Sec. III-C.4): afterwards position p
+  holds the qubit that was at position order[p].
 
 Positions are MPS site indices: site 0 is the most significant bit of the
 statevector index (Sec. II-A.1 tensor-product order).
@@ -205,6 +207,58 @@ def grid_rcs(rows, cols, cycles, seed, pattern="ABCDCDAB", singles="paper"):
             pb = snake_position(b[0], b[1], cols)
             ops.append(("2q", pa, pb, f))
     return ops
+
+
+def column_snake_position(r, c, rows):
+    """1D position of grid qubit (r, c) in the column-snake embedding, where the
+    vertical couplers (r, c)-(r+1, c) are chain neighbours."""
+    return c * rows + (r if c % 2 == 0 else rows - 1 - r)
+
+
+def embedding_change(rows, cols, cur, new):
+    """order of the site permutation from embedding ``cur`` to ``new`` (each a
+    function (r, c) -> position): new position p receives the qubit now at order[p]."""
+    order = [0] * (rows * cols)
+    for r in range(rows):
+        for c in range(cols):
+            order[new(r, c)] = cur(r, c)
+    return order
+
+
+def grid_rcs_permuted(rows, cols, cycles, seed, pattern="ABCDCDAB", singles="paper"):
+    """The circuit of ``grid_rcs`` (same seed, same gates) with the paper's
+    permutation approach to the vertical couplers (Sec. III-D.2): horizontal
+    patterns (A, B) run in the row-snake embedding and vertical ones (C, D) in the
+    column-snake embedding, where every coupler is a nearest-neighbour pair; a
+    ("perm", order) layer changes the embedding between them, and a last one
+    restores the row snake, so the final state is that of ``grid_rcs``."""
+    rng = np.random.default_rng(seed)
+    paper = [G.sqrt_x(), G.sqrt_y(), G.sqrt_w()]
+    f = G.fsim()
+    row = lambda r, c: snake_position(r, c, cols)  # noqa: E731
+    col = lambda r, c: column_snake_position(r, c, rows)  # noqa: E731
+    cur = row
+    ops = []
+    for cyc in range(cycles):
+        pat = pattern[cyc % len(pattern)]
+        want = row if pat in "AB" else col
+        for r in range(rows):
+            for c in range(cols):
+                u = paper[int(rng.integers(0, 3))] if singles == "paper" else G.haar_unitary(rng, 2)
+                ops.append(("1q", cur(r, c), u))
+        if want is not cur:
+            ops.append(("perm", embedding_change(rows, cols, cur, want)))
+            cur = want
+        for (a, b) in grid_pattern(rows, cols, pat):
+            ops.append(("2q", cur(*a), cur(*b), f))
+    if cur is not row:
+        ops.append(("perm", embedding_change(rows, cols, cur, row)))
+    return ops
+
+
+def inversions(order):
+    """Number of pairs p < q with order[p] > order[q]: the SWAP count of a bubble sort."""
+    return sum(1 for p in range(len(order)) for q in range(p + 1, len(order)) if order[p] > order[q])
 
 
 def count_two_qubit(ops):
