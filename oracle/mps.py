@@ -31,6 +31,17 @@ it.  Every step follows the paper's description:
   of the conjugate transpose; L is multiplied into the previous site), without
   truncation; after the gate the centre is site i+1.  The "local" policy never
   moves the centre.
+* MPO application (Sec. III-C.3, zip-up): an operator W_first ... W_last with
+  tensors W[a, b, out, in] (a = 1 on the first, b = 1 on the last) is contracted
+  into the sites left to right: with the carried matrix C[kk, a, l] (identity at
+  the start), Z[kk, out, b, r] = sum W[a, b, out, in] C[kk, a, l] A[l, in, r];
+  Z as the (2 kk) x (b r) matrix is split by the truncated pivoted QR, Q becomes
+  the site and R P^T the next carried C; the last Z is the last site.  The new
+  bond is capped at min(chi_max, 2 cap) with cap = min(2^b, 2^(n-b), chi_max),
+  the chain's physical bound, so one MPO of bond 2 never truncates for lack of
+  room; afterwards every bond of the range above its physical bound is brought
+  back to it by a split of the identity two-site gate, right to left (exact
+  under the canonical policy, where the cut's Schmidt rank is at most cap).
 * Amplitude: <x|psi> = A_0[:, x_0, :] A_1[:, x_1, :] ... (1x1 product).
 * Norm fidelity (Sec. III-E): F = <psi|psi> by transfer matrices
   E <- sum_s A[:, s, :]^H E A[:, s, :].
@@ -51,6 +62,13 @@ def _swap_gate():
 
 
 SWAP = _swap_gate()
+IDENTITY4 = np.eye(4, dtype=np.complex128)
+
+
+def physical_bond(n, b, chi):
+    """Largest Schmidt rank across cut b of an n-qubit chain, capped at chi."""
+    e = min(b, n - b)
+    return chi if e >= 30 else min(2**e, chi)
 
 
 class OracleMPS:
@@ -147,6 +165,48 @@ class OracleMPS:
         self.n_two_site += 1
         return disc
 
+    def apply_mpo(self, first, ws, chi_max=None):
+        """Zip-up application of the MPO ``ws`` (list of W[a, b, out, in]) to the sites
+        first .. first+len(ws)-1; returns the discarded weights of its splits."""
+        chi = self.chi_max if chi_max is None else min(chi_max, self.chi_max)
+        ws = [np.asarray(w, dtype=np.complex128) for w in ws]
+        last = first + len(ws) - 1
+        assert ws[0].shape[0] == 1 and ws[-1].shape[1] == 1
+        if len(ws) == 1:
+            self.apply_1q(first, ws[0][0, 0])
+            return []
+        if self.policy == "canon":
+            self.move_centre(first)
+        n = self.n
+        discs = []
+        cl = self.sites[first].shape[0]
+        c = np.eye(cl, dtype=np.complex128).reshape(cl, 1, cl)  # C[kk, a, l]
+        for j, w in enumerate(ws):
+            i = first + j
+            y = np.einsum("kal,lsr->kasr", c, self.sites[i])
+            z = np.einsum("abts,kasr->ktbr", w, y)
+            kk, _, bd, cr = z.shape
+            if i == last:
+                self.sites[i] = np.ascontiguousarray(z.reshape(kk, 2, cr))
+                break
+            cap = min(chi, 2 * physical_bond(n, i + 1, chi))
+            q, r, jpvt, disc = _qr.cpqr(z.reshape(2 * kk, bd * cr), kmax=cap, pivot=True)
+            k = q.shape[1]
+            right = np.zeros((k, bd * cr), dtype=np.complex128)
+            right[:, jpvt] = r
+            self.sites[i] = np.ascontiguousarray(q).reshape(kk, 2, k)
+            c = right.reshape(k, bd, cr)
+            self.discarded.append(disc)
+            self.n_two_site += 1
+            discs.append(disc)
+        if self.policy == "canon":
+            self.centre = last
+        for b in range(last, first, -1):
+            cap = physical_bond(n, b, chi)
+            if self.sites[b].shape[0] > cap:
+                discs.append(self.apply_2q(b - 1, IDENTITY4, cap))
+        return discs
+
     def swap(self, i, chi_max=None):
         return self.apply_2q(i, SWAP, chi_max)
 
@@ -194,6 +254,8 @@ class OracleMPS:
                 self.apply_1q(op[1], op[2])
             elif op[0] == "perm":
                 self.permute(op[1], chi_max)
+            elif op[0] == "mpo":
+                self.apply_mpo(op[1], op[2], chi_max)
             else:
                 self.apply_2q_routed(op[1], op[2], op[3], chi_max)
 

@@ -38,6 +38,25 @@ def permute(v, n, order):
     return np.transpose(v.reshape([2] * n), list(order)).reshape(-1)
 
 
+def mpo_matrix(ws):
+    """Dense operator of an MPO (W[a, b, out, in] per site, first site most
+    significant): sum over the bonds of the tensor products of W[a, b]."""
+    m = np.asarray(ws[0])[0]  # (b, out, in)
+    for w in ws[1:]:
+        w = np.asarray(w)
+        m = np.einsum("bxy,bczw->cxzyw", m, w)
+        d = m.shape[1] * m.shape[2]
+        m = m.reshape(w.shape[1], d, d)
+    return m[0]
+
+
+def apply_mpo(v, n, first, ws):
+    """MPO on the qubits first .. first+len(ws)-1 as a dense operator."""
+    L = len(ws)
+    t = v.reshape(2**first, 2**L, 2 ** (n - first - L))
+    return np.einsum("ab,xby->xay", mpo_matrix(ws), t).reshape(-1)
+
+
 def run(ops, n, v=None):
     if v is None:
         v = zero_state(n)
@@ -46,6 +65,8 @@ def run(ops, n, v=None):
             v = apply_1q(v, n, op[1], op[2])
         elif op[0] == "perm":
             v = permute(v, n, op[1])
+        elif op[0] == "mpo":
+            v = apply_mpo(v, n, op[1], op[2])
         else:
             v = apply_2q(v, n, op[1], op[2], op[3])
     return v

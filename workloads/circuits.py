@@ -8,6 +8,8 @@ A circuit is a list of operations:
   consumer routes non-adjacent pairs with SWAP chains (Sec. III-C.4).
 * ``("perm", order)``    site permutation (Sec. III-C.4): afterwards position p
   holds the qubit that was at position order[p].
+* ``("mpo", first, ws)`` matrix product operator on positions first ..
+  first+len(ws)-1, ws[j] of shape (a, b, 2, 2) = W[left bond, right bond, out, in].
 
 Positions are MPS site indices: site 0 is the most significant bit of the
 statevector index (Sec. II-A.1 tensor-product order).
@@ -97,6 +99,44 @@ def iqft_noswap(qubits):
     for j in range(t - 1, -1, -1):
         for k in range(t - j, 1, -1):
             ops.append(("2q", qubits[j + k - 1], qubits[j], _cphase_k(k, -1)))
+        ops.append(("1q", qubits[j], G.hadamard()))
+    return ops
+
+
+def controlled_phase_mpo(phases):
+    """MPO (bond 2) of the controlled phases of one control qubit (Sec. III-D.1): the
+    control on the first site, targets on the following ones with phase shifts
+    diag(1, exp(i phases[k])).  W_first = (Pi_0, Pi_1), W_mid = diag(I, P), W_last =
+    (I, P)^T, so the operator is Pi_0 (x) I ... + Pi_1 (x) P_1 (x) P_2 ..."""
+    eye = np.eye(2, dtype=np.complex128)
+    pi0 = np.diag([1.0, 0.0]).astype(np.complex128)
+    pi1 = np.diag([0.0, 1.0]).astype(np.complex128)
+    first = np.zeros((1, 2, 2, 2), dtype=np.complex128)
+    first[0, 0], first[0, 1] = pi0, pi1
+    ws = [first]
+    for k, ph in enumerate(phases):
+        p = np.diag([1.0, np.exp(1j * ph)]).astype(np.complex128)
+        if k < len(phases) - 1:
+            w = np.zeros((2, 2, 2, 2), dtype=np.complex128)
+            w[0, 0], w[1, 1] = eye, p
+        else:
+            w = np.zeros((2, 1, 2, 2), dtype=np.complex128)
+            w[0, 0], w[1, 0] = eye, p
+        ws.append(w)
+    return ws
+
+
+def iqft_mpo(qubits):
+    """``iqft_noswap`` with the controlled phases of each qubit merged into one MPO of
+    bond 2 (Sec. III-D.1): for j = t-1 .. 0 the MPO on positions qubits[j] ..
+    qubits[t-1] (consecutive) with phases -2 pi / 2^k on qubits[j+k-1], then H on
+    qubits[j]."""
+    t = len(qubits)
+    assert list(qubits) == list(range(qubits[0], qubits[0] + t)), "positions must be consecutive"
+    ops = []
+    for j in range(t - 1, -1, -1):
+        if j < t - 1:
+            ops.append(("mpo", qubits[j], controlled_phase_mpo([-2 * np.pi / 2**k for k in range(2, t - j + 1)])))
         ops.append(("1q", qubits[j], G.hadamard()))
     return ops
 
