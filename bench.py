@@ -661,6 +661,54 @@ def truncation_workload(args):
                       "gate_rows": gate_rows}), flush=True)
 
 
+def iqft_workload(args):
+    """Random-saturation IQFT (Sec. IV-D.1, the IQFT output-fidelity study; Sec. III-D.1): an
+    n-qubit random mixed-canonical state whose bonds are filled to a fraction sigma of
+    chi_max (bond min(chain bound, sigma chi)), then the IQFT on all qubits as one
+    controlled-phase MPO of bond 2 per qubit, applied by zip-up, CANON policy.  Per
+    sigma and precision: CUDA-synchronised seconds, the norm fidelity after the IQFT,
+    and the splits (zip-up + recompression).  For the smallest sigma the gate-by-gate
+    IQFT (controlled phases routed by SWAP chains) is timed too."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from workloads import circuits, states
+
+    __graft_entry__.build()
+    from paper_2505_06119_gb300 import MPS
+
+    n, chi = args.iqft_n, args.iqft_chi
+    sigmas = [float(x) for x in args.iqft_sigma.split(",") if x]
+    mpo_ops = circuits.iqft_mpo(list(range(n)))
+    gate_ops = circuits.iqft_noswap(list(range(n)))
+    rows = []
+    for sg in sigmas:
+        fill = max(1, int(round(sg * chi)))
+        bonds = [min(b, fill) for b in states.max_bond_dims(n, chi)]
+        sites = states.random_canonical_mps(n, bonds, 0, seed=5)
+        runs = [("mpo", mpo_ops, p) for p in ("mixed", "fp64")]
+        if sg == min(sigmas):
+            runs.append(("gates", gate_ops, "mixed"))
+        for how, ops, prec in runs:
+            with MPS(n, chi, precision=prec, policy="canon") as m:
+                m.set_sites(sites, centre=0)
+                d0, c0 = m.discarded()
+                m.sync()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                m.run(ops)
+                m.sync()
+                dt = time.perf_counter() - t
+                d1, c1 = m.discarded()
+                rows.append({"sigma": sg, "input_bond": max(bonds), "iqft": how, "precision": prec, "seconds": dt,
+                             "norm_fidelity": m.fidelity(), "splits": c1 - c0, "discarded_sum": d1 - d0,
+                             "max_bond": max(m.bond_dims())})
+    print(json.dumps({"workload": "iqft", "n": n, "chi_max": chi,
+                      "input": "random mixed-canonical MPS, bonds min(chain bound, sigma chi_max), seed 5",
+                      "rows": rows}), flush=True)
+
+
 def big_gate_workload(args):
     """One two-site apply at the paper's largest bond dimension (chi_l = chi_m = chi_r =
     args.big_chi, theta (2 chi)^2; the scope table's M5 timing), mixed path, through the
@@ -732,11 +780,15 @@ def main():
     ap.add_argument("--cpu-chi", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-overlap", action="store_true")
-    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit", "big", "truncation"],
+    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit", "big", "truncation", "iqft"],
                     help="gate: the headline metric; layer: batched vs one-by-one layer times; "
                          "circuit: whole-circuit throughput and fidelity deviation; "
                          "big: one apply at a large bond dimension; "
-                         "truncation: pivoted QR vs SVD splits (fidelity, runtime)")
+                         "truncation: pivoted QR vs SVD splits (fidelity, runtime); "
+                         "iqft: random-saturation IQFT by controlled-phase MPOs")
+    ap.add_argument("--iqft-n", type=int, default=20)
+    ap.add_argument("--iqft-chi", type=int, default=128)
+    ap.add_argument("--iqft-sigma", default="0.125,0.25,0.5,1.0")
     ap.add_argument("--trunc-n", type=int, default=16)
     ap.add_argument("--trunc-depth", type=int, default=16)
     ap.add_argument("--trunc-chi", default="8,16,32")
@@ -755,6 +807,8 @@ def main():
         big_gate_workload(args)
     elif args.workload == "truncation":
         truncation_workload(args)
+    elif args.workload == "iqft":
+        iqft_workload(args)
     elif args.impl == "reference":
         reference(args)
     else:

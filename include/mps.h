@@ -184,6 +184,23 @@ int mps_permute(mps_t h, const int* order, int chi_max, long long* swaps);
  * mps_apply_2q.  chi_max as for mps_apply_2q. */
 int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count, int chi_max);
 
+/* Matrix product operator on sites first .. first+count-1, applied by zip-up
+ * (Sec. III-C.3; the IQFT's controlled-phase MPOs of Sec. III-D.1 have bond 2).
+ * bonds[0..count] are the MPO's bond dims: bonds[0] = bonds[count] = 1 and
+ * 1 <= bonds[j] <= 2 (larger: MPS_E_UNSUPPORTED).  W holds the site tensors one
+ * after another, site j as W_j[a][b][out][in] (a < bonds[j], b < bonds[j+1],
+ * row-major, bonds[j] * bonds[j+1] * 4 entries).  Left to right, the carried block
+ * times site j and W_j form Z[(kk, out), (b, r)], which the truncated pivoted QR
+ * splits (Q to the site, R P^T carried on; k = min(rows, columns, chi_max, room));
+ * the last Z is the last site.  The room reserved for a bond is twice the chain's
+ * bound min(2^b, 2^(n-b), chi_max) (at most chi_max), so one MPO of bond 2 is never
+ * truncated for lack of room; bonds left above the chain's bound are then brought
+ * back to it by splitting the identity two-site gate, right to left (exact under
+ * the canonical policy).  Under MPS_POLICY_CANON the centre is moved to `first`
+ * before and is at the last recompressed site (or `last`) after.  count = 1 applies
+ * W_0[0][0] as a one-qubit gate.  chi_max <= 0: the handle's.  Asynchronous. */
+int mps_apply_mpo(mps_t h, int first, int count, const int* bonds, const mps_c128* W, int chi_max);
+
 /* <bits|psi> = A_0[:, b_0, :] A_1[:, b_1, :] ... (bits[i] in {0,1} for site i).
  * Synchronous. */
 int mps_amplitude(mps_t h, const uint8_t* bits, mps_c128* out);

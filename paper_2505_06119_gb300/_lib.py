@@ -88,6 +88,7 @@ SIGNATURES = {
     "mps_move_centre": (_I, [_P, _I]),
     "mps_discarded_weight": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "mps_svd_last_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)]),
+    "mps_apply_mpo": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(mps_c128), _I]),
     "mps_set_stream": (_I, [_P, _P]),
     "mps_sync": (_I, [_P]),
     "mps_last_error": (ctypes.c_char_p, [_P]),

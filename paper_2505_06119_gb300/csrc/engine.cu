@@ -400,6 +400,10 @@ struct mps_s {
   void* actx = nullptr;
   std::vector<void*> allocs;
   std::vector<int> bond, capb;  // bond dims, reserved bond dims
+  std::vector<int> physb;       // min(2^b, 2^(n-b), chi_max): the chain's Schmidt-rank bound
+  // MPO zip-up scratch (lazy): carried block C and the product Y = C A
+  char* mpo_ws = nullptr;
+  size_t mpo_half = 0;
   std::vector<char*> site;
   int centre = 0;
   size_t esz = 16;
@@ -655,6 +659,120 @@ int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
   h->bond[i + 1] = k;
   h->nsplit++;
   if (h->policy == MPS_POLICY_CANON) h->centre = i + 1;
+  return MPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// MPO application by zip-up (Sec. III-C.3).  Left to right over the MPO's
+// sites: Y = C A_i (C carried from the previous split, identity at the first
+// site), Z = W_i contracted into Y, Z split by the truncated pivoted QR (Q to the
+// site, R P^T carried on); the last Z is the last site.  The new bond is capped
+// by the reserved room (twice the chain's bound), and bonds left above the
+// chain's bound are brought back to it by identity-gate splits, right to left.
+constexpr mps_c128 kIdentity4[16] = {{1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0},
+                                     {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}};
+
+template <typename T>
+int apply_1q_t(mps_t h, int q, const mps_c128* u);
+
+int mpo_ready(mps_t h) {
+  if (h->mpo_ws) return MPS_OK;
+  h->mpo_half = align_up(h->esz * (size_t)(2 * h->chicap) * (2 * h->chicap));
+  h->mpo_ws = (char*)dev_alloc(h, 2 * h->mpo_half);
+  if (!h->mpo_ws) return fail(h, MPS_E_NOMEM, "apply_mpo: scratch");
+  return MPS_OK;
+}
+
+template <typename T>
+int apply_mpo_t(mps_t h, int first, int count, const int* bonds, const mps_c128* W, int chi) {
+  if (count == 1) return apply_1q_t<T>(h, first, W);  // W[0][0] is the 2 x 2 operator (out, in)
+  int rc = mpo_ready(h);
+  if (rc) return rc;
+  if (h->policy == MPS_POLICY_CANON) {
+    rc = move_centre_t<T>(h, first);
+    if (rc) return rc;
+  }
+  Ws<T> w = views<T>(h);
+  LaunchHooks* hk = &h->prof.hooks;
+  T* Y = (T*)h->mpo_ws;
+  T* C = (T*)(h->mpo_ws + h->mpo_half);
+  const int last = first + count - 1;
+  int kk = h->bond[first], adim = 1;
+  int cl = h->bond[first];  // left bond of site i as stored (bond[i] already holds the new k)
+  const mps_c128* wj = W;
+  for (int j = 0; j < count; ++j) {
+    const int i = first + j;
+    const int cr = h->bond[i + 1], bdim = bonds[j + 1];
+    MpoTensor<T> wt;
+    for (int e = 0; e < 16; ++e) wt.w[e] = mk<typename real_of<T>::type>(0, 0);
+    for (int a = 0; a < adim; ++a)
+      for (int b = 0; b < bdim; ++b)
+        for (int o = 0; o < 4; ++o) {
+          const mps_c128 x = wj[(a * bdim + b) * 4 + o];
+          wt.w[(a * 2 + b) * 4 + o] = mk<typename real_of<T>::type>((typename real_of<T>::type)x.re,
+                                                                    (typename real_of<T>::type)x.im);
+        }
+    wj += adim * bdim * 4;
+    const T* ysrc = (const T*)h->site[i];
+    int64_t yr = 2 * (int64_t)cr, yc = 1;
+    int nl = 1;
+    hook_before(hk, MPS_KCLASS_THETA, 0, j ? 8.0 * kk * adim * 2.0 * cr * cl : 0);
+    if (j > 0) {
+      // Y (column-major, (kk adim) x (2 cr)) = C (row-major (kk adim) x cl) . A_i (row-major cl x 2 cr)
+      GemmDesc<T> d;
+      d.M = kk * adim;
+      d.N = 2 * cr;
+      d.K = cl;
+      d.alpha = mk<typename real_of<T>::type>(1, 0);
+      d.beta = mk<typename real_of<T>::type>(0, 0);
+      d.A = C;
+      d.lda = cl;
+      d.a_row = 1;
+      d.B = (const T*)h->site[i];
+      d.ldb = 2 * cr;
+      d.b_row = 1;
+      d.C = Y;
+      d.ldc = d.M;
+      cudaError_t e = gemm_simt<T>(d, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "apply_mpo: carried product");
+      nl += gemm_launches(d);
+      ysrc = Y;
+      yr = 1;
+      yc = d.M;
+    }
+    if (i == last) {
+      cudaError_t e = mpo_contract<T>(ysrc, yr, yc, kk, adim, 1, cr, wt, (T*)h->site[i], 0, 1, h->stream);
+      hook_after(hk, MPS_KCLASS_THETA, nl);
+      if (e != cudaSuccess) return cuda_fail(h, e, "apply_mpo: last site");
+      break;
+    }
+    cudaError_t e = mpo_contract<T>(ysrc, yr, yc, kk, adim, bdim, cr, wt, w.W, w.ldw, 0, h->stream);
+    hook_after(hk, MPS_KCLASS_THETA, nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply_mpo: contraction");
+    const int m = 2 * kk, nn = bdim * cr;
+    const int k = std::min(std::min(m, nn), std::min(chi, h->capb[i + 1]));
+    double* slot = h->d_disclog + (h->nsplit % kDiscLog);
+    QrPlan<T> p = make_plan<T>(w, h->kn, m, nn, k, 1, slot, h->d_scalar + 1);
+    e = qr_factor<T>(p, h->stream, hk);
+    if (e == cudaSuccess) e = qr_form_q<T>(p, w.Q, w.ldq, h->stream, hk);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply_mpo: split");
+    hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * ((double)m * k + (double)k * nn) * sizeof(T), 0);
+    e = transpose_copy<T>(w.Q, w.ldq, (T*)h->site[i], k, k, m, 0, h->stream);
+    if (e == cudaSuccess) e = split_right<T>(w.W, w.ldw, w.jpvt, w.inv, k, nn, C, h->stream);
+    hook_after(hk, MPS_KCLASS_SPLIT, 3);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply_mpo: split");
+    h->bond[i + 1] = k;
+    h->nsplit++;
+    kk = k;
+    adim = bdim;
+    cl = cr;
+  }
+  if (h->policy == MPS_POLICY_CANON) h->centre = last;
+  for (int b = last; b > first; --b) {
+    if (h->bond[b] <= h->physb[b]) continue;
+    rc = apply_2q_t<T>(h, b - 1, kIdentity4, h->physb[b]);
+    if (rc) return rc;
+  }
   return MPS_OK;
 }
 
@@ -1119,8 +1237,12 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   h->bond.assign(n + 1, 1);
   h->capb.resize(n + 1);
   int chicap = 1;
+  // reserved bonds: twice the chain's bound (at most chi_max), the room an MPO of
+  // bond 2 needs while it is zipped up; the outer bonds stay 1
+  h->physb.resize(n + 1);
   for (int b = 0; b <= n; ++b) {
-    h->capb[b] = max_bond(n, b, chi_max);
+    h->physb[b] = max_bond(n, b, chi_max);
+    h->capb[b] = (b == 0 || b == n) ? 1 : (int)std::min<int64_t>(2 * (int64_t)h->physb[b], chi_max);
     chicap = std::max(chicap, h->capb[b]);
   }
   h->chicap = chicap;
@@ -1331,6 +1453,22 @@ int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count,
   if (chi_max <= 0) chi_max = h->chi_max;
   return h->prec == MPS_PREC_FP64 ? layer_t<c128>(h, sites, gates, count, chi_max)
                                   : layer_t<c64>(h, sites, gates, count, chi_max);
+}
+
+int mps_apply_mpo(mps_t h, int first, int count, const int* bonds, const mps_c128* W, int chi_max) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!bonds || !W || count < 1 || first < 0 || first + count > h->n)
+    return fail(h, MPS_E_ARG, "apply_mpo: bad range or null pointer");
+  if (bonds[0] != 1 || bonds[count] != 1) return fail(h, MPS_E_ARG, "apply_mpo: outer MPO bonds must be 1");
+  for (int j = 1; j < count; ++j) {
+    if (bonds[j] < 1) return fail(h, MPS_E_ARG, "apply_mpo: MPO bond below 1");
+    if (bonds[j] > 2) return fail(h, MPS_E_UNSUPPORTED, "apply_mpo: MPO bonds above 2 are not supported");
+  }
+  if (chi_max > h->chi_max) return fail(h, MPS_E_ARG, "apply_mpo: chi_max above the handle's");
+  int chi = chi_max <= 0 ? h->chi_max : chi_max;
+  return h->prec == MPS_PREC_FP64 ? apply_mpo_t<c128>(h, first, count, bonds, W, chi)
+                                  : apply_mpo_t<c64>(h, first, count, bonds, W, chi);
 }
 
 int mps_amplitude(mps_t h, const uint8_t* bits, mps_c128* out) {

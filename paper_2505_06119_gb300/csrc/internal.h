@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -178,6 +179,19 @@ inline void hook_before(LaunchHooks* h, int kclass, double bytes, double flops) 
 inline void hook_after(LaunchHooks* h, int kclass, int nlaunch) {
   if (h && h->after) h->after(h, kclass, nlaunch);
 }
+
+// ---------------------------------------------------------------------------
+// MPO zip-up contraction (mpo.cu; Sec. III-C.3): tensor W[a][b][out][in] with
+// a, b < 2, element ((a*2 + b)*2 + out)*2 + in; unused bond entries are zero.
+template <typename T>
+struct MpoTensor {
+  T w[16];
+};
+// Z[(kk,out),(b,r)] = sum_{a,in} W[a][b][out][in] Y[(kk*adim + a)*ys_row + (in*cr + r)*ys_col];
+// Z column-major (ldz), or, with to_site (bdim == 1), the row-major site (kk, 2, cr)
+template <typename T>
+cudaError_t mpo_contract(const T* Y, int64_t ys_row, int64_t ys_col, int kk, int adim, int bdim, int cr,
+                         const MpoTensor<T>& W, T* Z, int64_t ldz, int to_site, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Truncated SVD split by one-sided Jacobi (svd.cu; Sec. III-B.2 Table III).

@@ -105,6 +105,14 @@ class MPS:
         g = _gate(np.concatenate([np.asarray(x).reshape(-1) for x in gates]) if cnt else np.zeros(16), 16 * max(cnt, 1))
         self._check(self.lib.mps_apply_layer(self.h, s, g, cnt, chi_max))
 
+    def apply_mpo(self, first, ws, chi_max=0):
+        """MPO (list of W[a, b, out, in] arrays) on sites first .. first+len(ws)-1."""
+        ws = [np.asarray(x, dtype=np.complex128) for x in ws]
+        bonds = [w.shape[0] for w in ws] + [ws[-1].shape[1]]
+        flat = np.concatenate([np.ascontiguousarray(w).reshape(-1) for w in ws])
+        b = (ctypes.c_int * len(bonds))(*bonds)
+        self._check(self.lib.mps_apply_mpo(self.h, first, len(ws), b, _gate(flat, flat.size), chi_max))
+
     def permute(self, order, chi_max=0):
         """Site permutation by bubble-sorted SWAPs: position p ends up holding the site
         now at order[p].  Returns the number of SWAPs."""
@@ -119,6 +127,8 @@ class MPS:
                 self.apply_1q(op[1], op[2])
             elif op[0] == "perm":
                 self.permute(op[1], chi_max)
+            elif op[0] == "mpo":
+                self.apply_mpo(op[1], op[2], chi_max)
             elif abs(op[1] - op[2]) == 1 and op[1] < op[2]:
                 self.apply_2q(op[1], op[3], chi_max)
             else:
