@@ -87,6 +87,15 @@ struct PanelArgs {
   int bulk;    // phase D streams column chunks with bulk asynchronous copies
 };
 
+// Squared column norm below which a reflector is the identity (tau = 0): in
+// complex64, 1/(alpha - beta) of such a column would not fit the data type (its
+// entries are below FLT_MIN, rounding residue of exact zeros), and rounding it to
+// FP32 would give inf and then NaN in v.  Complex128 keeps every nonzero column.
+template <typename T>
+__device__ __forceinline__ double zero_column_level() {
+  return sizeof(T) == 8 ? 1.3814317e-76 : 0.0;  // FLT_MIN^2
+}
+
 // Pivot key of a squared norm: for a non-negative double (or +inf) its bit
 // pattern orders like its value, so pivots are compared as 64-bit integers
 // (exact, and off the FP64 pipe); NaN or negative values map to -1 and never win.
@@ -558,7 +567,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       xn = warp_sum(xn);
       if (lane == 0) {
         c128 tau, sc, beta;
-        if (xn == 0.0 && al.im == 0.0) {
+        if ((xn == 0.0 && al.im == 0.0) || al.re * al.re + al.im * al.im + xn < zero_column_level<T>()) {
           tau = mk<double>(0, 0);
           sc = mk<double>(0, 0);
           beta = al;
@@ -986,7 +995,7 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
         const double xn = v0;
         const c128 al = mk<double>(v1, v2);
         c128 tau, sc, beta;
-        if (xn == 0.0 && al.im == 0.0) {
+        if ((xn == 0.0 && al.im == 0.0) || al.re * al.re + al.im * al.im + xn < zero_column_level<T>()) {
           tau = mk<double>(0, 0);
           sc = mk<double>(0, 0);
           beta = al;
