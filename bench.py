@@ -145,8 +145,8 @@ class ClockSampler:
 # algorithmic bytes (both are sums over the trailing block), so a launch's traffic is
 # this ratio times its algorithmic bytes.  Valid only for the kernel source it was
 # measured on (sha256 of csrc/qr.cu); otherwise reported as null.
-PANEL_NCU = {"qr_cu_sha256": "8dfeb07d03c8b49c09dc2370a6ace3b1756c8f93a9ec26926d430f3cd56a2d2c",
-             "dram_over_algorithmic": 0.9885}
+PANEL_NCU = {"qr_cu_sha256": "3b4f929abb7c11b6968f3c418be998f909aa72a659af441ccb9a3e4952cae2db",
+             "dram_over_algorithmic": 0.9896}
 
 
 def panel_traffic(alg_bytes_per_launch):
