@@ -300,6 +300,32 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
     for (int g = 0; g < RG; ++g) {
       const int i = i0 + 32 * g + 2 * tm;
       if (i >= d.M) continue;
+      const bool pair = i + 1 < d.M;
+      // C of this row group, all loads issued before the group's first store (a
+      // store to C could alias a later load, so the compiler would otherwise keep
+      // each load behind the previous store and pay one memory latency per pair)
+      float4 cin[4][2];
+      if constexpr (beta_nz) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+#pragma unroll
+          for (int f = 0; f < 2; ++f) {
+            const int j = j0 + 32 * h + 2 * tn + f;
+            cin[h][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j >= d.N) continue;
+            const c64* cp = dst + i + (int64_t)j * ldd;
+            if (dvec && pair) {
+              cin[h][f] = *reinterpret_cast<const float4*>(cp);
+            } else {
+              cin[h][f].x = cp[0].re;
+              cin[h][f].y = cp[0].im;
+              if (pair) {
+                cin[h][f].z = cp[1].re;
+                cin[h][f].w = cp[1].im;
+              }
+            }
+          }
+      }
 #pragma unroll
       for (int h = 0; h < 4; ++h)
 #pragma unroll
@@ -307,7 +333,6 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
           const int j = j0 + 32 * h + 2 * tn + f;
           if (j >= d.N) continue;
           c64* cp = dst + i + (int64_t)j * ldd;
-          const bool pair = i + 1 < d.M;
           c64 v0 = mk<float>(acc[2 * g][2 * h + f][0], acc[2 * g][2 * h + f][1]);
           c64 v1 = mk<float>(acc[2 * g + 1][2 * h + f][0], acc[2 * g + 1][2 * h + f][1]);
           if (!alpha_one) {
@@ -315,17 +340,8 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
             v1 = d.alpha * v1;
           }
           if constexpr (beta_nz) {  // C = alpha sum + beta C, the sum rounded on its own first
-            c64 c0, c1 = mk<float>(0.f, 0.f);
-            if (dvec && pair) {
-              const float4 q = *reinterpret_cast<const float4*>(cp);
-              c0 = mk<float>(q.x, q.y);
-              c1 = mk<float>(q.z, q.w);
-            } else {
-              c0 = cp[0];
-              if (pair) c1 = cp[1];
-            }
-            v0 = v0 + d.beta * c0;
-            v1 = v1 + d.beta * c1;
+            v0 = v0 + d.beta * mk<float>(cin[h][f].x, cin[h][f].y);
+            v1 = v1 + d.beta * mk<float>(cin[h][f].z, cin[h][f].w);
           }
           if (dvec && pair) {
             *reinterpret_cast<float4*>(cp) = make_float4(v0.re, v0.im, v1.re, v1.im);
