@@ -48,7 +48,7 @@ namespace mpsg {
 namespace {
 
 constexpr int kJMaxWarps = 8;  // warps (pairs in flight) per CTA, at most
-constexpr int kChunk = 8;  // elements per lane summed in the data precision before FP64
+constexpr int kChunk = 8;  // elements per lane summed (and loaded) together before the running sum
 
 template <typename T>
 struct JacobiArgs {
