@@ -47,6 +47,23 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) <= set(_lib.SIGNATURES)
 
 
+def test_binding_arity_matches_the_header():
+    """Every prototype in include/*.h has a binding signature with the same number of
+    parameters, so a ctypes call can never shift its arguments."""
+    from paper_2505_06119_gb300 import _lib
+
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", fn)).read(), flags=re.S)
+        protos = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(mps_\w+)\s*\(([^)]*)\)\s*;", src, flags=re.M)
+        assert protos
+        for name, args in protos:
+            args = args.strip()
+            n = 0 if args in ("", "void") else len([a for a in args.split(",") if a.strip()])
+            assert len(_lib.SIGNATURES[name][1]) == n, name
+
+
 def test_host_argument_checks(lib):
     from paper_2505_06119_gb300 import _lib as L
 
