@@ -53,6 +53,18 @@ def dist_env():
     return ws, rank, local
 
 
+def init_dist(backend):
+    """Process group of the replica run, with a bounded collective timeout
+    (MPS_BENCH_PG_TIMEOUT_S, default 600 s): a replica that dies or stalls before the
+    timing all-reduce makes the other ranks fail with an error instead of waiting."""
+    import datetime
+
+    import torch.distributed as dist
+
+    secs = float(os.environ.get("MPS_BENCH_PG_TIMEOUT_S", "600"))
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=secs))
+
+
 def make_state(chi, n, centre, seed):
     import numpy as np
 
@@ -179,9 +191,7 @@ def ours(args):
 
     ws, rank, local = dist_env()
     if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
+        init_dist("nccl")
     torch.cuda.set_device(local)
     __graft_entry__.build()
     from paper_2505_06119_gb300 import MPS

@@ -78,3 +78,40 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
 
     assert bench.reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+FAIL_WORKER = r"""
+import os, sys, time
+sys.path.insert(0, sys.argv[1])
+import bench
+rank = int(os.environ["RANK"])
+bench.init_dist("gloo")
+if rank == 1:
+    os._exit(3)                       # a replica dies before the timing all-reduce
+t0 = time.time()
+try:
+    bench.replica_throughput(1000.0, 1.0, steps=10, e2e_steps=1, ws=2, device="cpu")
+    print("no error", flush=True)
+except Exception as e:
+    print("error after %.1f s: %s" % (time.time() - t0, type(e).__name__), flush=True)
+    os._exit(7)
+"""
+
+
+def test_dead_replica_fails_the_others_instead_of_hanging():
+    """Host-side failure detection of the replica run: a rank that exits before the
+    all-reduce makes the survivor's collective raise within the process group's bounded
+    timeout (MPS_BENCH_PG_TIMEOUT_S), so the job ends with an error, not a hang."""
+    pytest.importorskip("torch.distributed")
+    port = free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
+                   MPS_BENCH_PG_TIMEOUT_S="10")
+        procs.append(subprocess.Popen([sys.executable, "-c", FAIL_WORKER, ROOT], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    out0, _ = procs[0].communicate(timeout=120)
+    procs[1].communicate(timeout=120)
+    assert procs[1].returncode == 3
+    assert procs[0].returncode == 7, out0
+    assert "error after" in out0
