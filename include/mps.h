@@ -49,8 +49,10 @@
  *     mps_get_site, mps_discarded_weight).  After such a failure the handle
  *     rejects further mutation with MPS_E_STATE; mps_last_error() describes it.
  *   - A handle is not thread-safe; distinct handles may be used from distinct
- *     threads.
- */
+ *     threads.  The first centre move of a precision picks, once per process,
+ *     whether its panels run on a thread-block cluster; if two threads make that
+ *     first call at the same moment one may take the (equally correct) grid
+ *     kernel, so runs that must be bitwise reproducible make it from one thread. */
 #ifndef MPS_GB300_H
 #define MPS_GB300_H
 

@@ -1355,17 +1355,12 @@ int mps_apply_2q(mps_t h, int site, const mps_c128 g[16], int chi_max) {
   return h->prec == MPS_PREC_FP64 ? apply_2q_t<c128>(h, site, g, chi) : apply_2q_t<c64>(h, site, g, chi);
 }
 
-static const mps_c128* swap_gate() {
-  static mps_c128 g[16];
-  static bool init = false;
-  if (!init) {
-    memset(g, 0, sizeof g);
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) g[(2 * b + a) * 4 + (2 * a + b)].re = 1.0;
-    init = true;
-  }
-  return g;
-}
+// SWAP: g[(2b+a)*4 + (2a+b)] = 1 (output (b, a) from input (a, b)); a constant table, so
+// handles on different threads share it without a first-use race
+constexpr mps_c128 kSwap4[16] = {{1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0},
+                                 {0, 0}, {1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}};
+
+static const mps_c128* swap_gate() { return kSwap4; }
 
 int mps_swap(mps_t h, int site, int chi_max) { return mps_apply_2q(h, site, swap_gate(), chi_max); }
 

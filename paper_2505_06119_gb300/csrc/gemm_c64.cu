@@ -356,13 +356,11 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
 
 template <int BM, bool THETA, bool BETA>
 cudaError_t launch(const GemmDesc<c64>& d, const ThetaEpi& te, dim3 grid, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_c64_kernel<BM, THETA, BETA>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem_bytes<BM>());
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // set once per instantiation; a function-local static is initialised thread-safely
+  static const cudaError_t attr = cudaFuncSetAttribute(gemm_c64_kernel<BM, THETA, BETA>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       g_smem_bytes<BM>());
+  if (attr != cudaSuccess) return attr;
   gemm_c64_kernel<BM, THETA, BETA><<<grid, G_NT, g_smem_bytes<BM>(), s>>>(d, te);
   return cudaGetLastError();
 }

@@ -41,6 +41,8 @@
 // round spread over all SMs (the FP64 work of a pair competes for the few FP64
 // units of an SM sub-partition).  The two V columns of a pair are prefetched
 // into L1 while the pair sums are formed, so their rotation does not wait on L2.
+#include <atomic>
+
 #include "internal.h"
 
 namespace mpsg {
@@ -331,12 +333,15 @@ __global__ void svd_right_kernel(const T* X, int64_t ldx, const int* perm, int M
 
 // launch shape of the Jacobi kernel for `pairs` pairs per round: warps per CTA so
 // that the pairs spread over every SM, CTAs capped by co-residency
+// (the co-residency per block size is cached in atomics: handles on different
+// threads may fill an entry at the same time, with the same value)
 template <typename T>
 void jacobi_shape(int pairs, int& G, int& warps) {
-  static int cap[2][kJMaxWarps + 1] = {};
+  static std::atomic<int> cap[2][kJMaxWarps + 1];
   const int sms = num_sms();
   warps = std::max(1, std::min(kJMaxWarps, (pairs + sms - 1) / sms));
-  int& c = cap[sizeof(T) == 8 ? 0 : 1][warps];
+  std::atomic<int>& slot = cap[sizeof(T) == 8 ? 0 : 1][warps];
+  int c = slot.load(std::memory_order_relaxed);
   if (c == 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, 32 * warps, 0) != cudaSuccess ||
@@ -345,6 +350,7 @@ void jacobi_shape(int pairs, int& G, int& warps) {
       per_sm = 1;
     }
     c = per_sm * sms;
+    slot.store(c, std::memory_order_relaxed);
   }
   G = std::max(1, std::min(c, (pairs + warps - 1) / warps));
 }
