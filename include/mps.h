@@ -199,8 +199,10 @@ int mps_apply_layer(mps_t h, const int* sites, const mps_c128* gates, int count,
  * truncated for lack of room; bonds left above the chain's bound are then brought
  * back to it by splitting the identity two-site gate, right to left (exact under
  * the canonical policy).  Under MPS_POLICY_CANON the centre is moved to `first`
- * before and is at the last recompressed site (or `last`) after.  count = 1 applies
- * W_0[0][0] as a one-qubit gate.  chi_max <= 0: the handle's.  Asynchronous. */
+ * before and is at the last recompressed site (or `last`) after.  The zip-up splits
+ * are pivoted QRs whatever the handle's truncation setting; the recompression splits
+ * follow it.  count = 1 applies W_0[0][0] as a one-qubit gate.  chi_max <= 0: the
+ * handle's.  Asynchronous. */
 int mps_apply_mpo(mps_t h, int first, int count, const int* bonds, const mps_c128* W, int chi_max);
 
 /* <bits|psi> = A_0[:, b_0, :] A_1[:, b_1, :] ... (bits[i] in {0,1} for site i).
