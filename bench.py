@@ -496,7 +496,8 @@ def layer_workload(args):
 
 
 def circuit_workload(args):
-    """Whole circuits (the scope table's M2 and, reduced, M3 workloads), mixed and FP64
+    """Whole circuits (the 40-qubit depth-20 brick-wall at chi 1024 and, reduced, the 7x7
+    grid random circuit), mixed and FP64
     paths under the canonical policy: two-qubit gate applies per second of each path
     (CUDA-synchronised wall clock over the whole circuit, routed gates counted once) and
     the mixed-vs-FP64 fidelity deviation at the end (both readings of the deviation:
@@ -721,7 +722,8 @@ def iqft_workload(args):
 
 def big_gate_workload(args):
     """One two-site apply at the paper's largest bond dimension (chi_l = chi_m = chi_r =
-    args.big_chi, theta (2 chi)^2; the scope table's M5 timing), mixed path, through the
+    args.big_chi, theta (2 chi)^2; the size of the quantum phase estimation circuit's central
+    gate), mixed path, through the
     raw-pointer C call on device buffers: Gaussian sites made on the GPU, seeded.  Checks
     the norm identity ||R P^T||^2 + discarded = ||theta||^2 with ||theta||^2 =
     sum (A^H A) .* conj(B B^H) (the gate is unitary on the physical indices)."""

@@ -49,10 +49,8 @@
  *     mps_get_site, mps_discarded_weight).  After such a failure the handle
  *     rejects further mutation with MPS_E_STATE; mps_last_error() describes it.
  *   - A handle is not thread-safe; distinct handles may be used from distinct
- *     threads.  The first centre move of a precision picks, once per process,
- *     whether its panels run on a thread-block cluster; if two threads make that
- *     first call at the same moment one may take the (equally correct) grid
- *     kernel, so runs that must be bitwise reproducible make it from one thread. */
+ *     threads, and on distinct devices.  What the library sets up at first use
+ *     (kernel attributes, occupancy, cluster sizes) is kept per device. */
 #ifndef MPS_GB300_H
 #define MPS_GB300_H
 
@@ -292,13 +290,26 @@ int mps_kernel_stats_reset(mps_t h);
  * chi_max) (Sec. III-C.2 with the split of Sec. III-B.2).  A_out may alias A
  * and B_out may alias B.  *discarded_dev (device double) receives the
  * discarded weight.  `workspace` must hold mps_two_site_workspace() bytes,
- * 256-byte aligned.  Asynchronous on `stream` (cudaStream_t, NULL = default). */
+ * 256-byte aligned.  Asynchronous on `stream` (cudaStream_t, NULL = default).
+ * The return code covers the host-side checks and the launches only.  These
+ * calls have no handle to carry a device-side failure (a bounded wait that
+ * expired, a failed check), so they report one by writing NaN to
+ * *discarded_dev, stream-ordered after the split; A_out and B_out are then
+ * undefined.  Callers that need to detect such failures pass discarded_dev. */
 int mps_two_site_workspace(int precision, int chi_l, int chi_m, int chi_r, int chi_max,
                            size_t* bytes);
 int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_max,
                        const void* A, const void* B, const mps_c128 g[16], void* A_out,
                        void* B_out, double* discarded_dev, void* workspace, size_t ws_bytes,
                        void* stream);
+
+/* Testing only: every later raw-pointer call (mps_two_site_apply and
+ * mps_two_site_apply_noalloc) bounds its device-side waits by timeout_s
+ * (0 = the default, 10 s) and makes its grid barriers wait for barrier_extra
+ * arrivals that never come (0 = normal operation), so a test can make a wait
+ * expire and see the NaN discarded weight.  Process-wide; MPS_E_ARG for
+ * negative values. */
+int mps_debug_raw_wait(int barrier_extra, double timeout_s);
 
 /* Workspace size of mps_two_site_apply_noalloc: 16 MiB. */
 #define MPS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
@@ -322,7 +333,9 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
  * does not order, race on it and must be serialised by the caller.
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture begins. */
+ * stream capture begins.  A device-side failure shows as a NaN discarded
+ * weight, as for mps_two_site_apply; the array's error word is cleared by the
+ * next call, so pass discarded_dev to see it. */
 int mps_two_site_apply_noalloc(int precision, int chi_l, int chi_m, int chi_r, int chi_max, const void* A,
                                const void* B, const mps_c128 g[16], void* A_out, void* B_out,
                                double* discarded_dev, void* stream);

@@ -99,6 +99,7 @@ SIGNATURES = {
                                 _P, _P, ctypes.c_size_t, _P]),
     "mps_two_site_apply_noalloc": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.POINTER(mps_c128), _P, _P,
                                         _P, _P]),
+    "mps_debug_raw_wait": (_I, [_I, ctypes.c_double]),
 }
 
 _lib = None

@@ -7,6 +7,7 @@
 // on the host (k = min(2 chi_l, 2 chi_r, chi_max)), so no step waits for the
 // device.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1055,6 +1056,17 @@ bool valid_site(mps_t h, int i) { return i >= 0 && i < h->n; }
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MPS_NOALLOC_SCRATCH_BYTES];
 
 namespace {
+// waits of the raw-pointer calls (mps_debug_raw_wait changes them for tests)
+constexpr unsigned long long kRawTimeoutNs = 10000000000ull;
+std::atomic<int> g_raw_barrier_extra{0};
+std::atomic<unsigned long long> g_raw_timeout_ns{kRawTimeoutNs};
+
+// after a raw-pointer split: a device-side failure (an expired bounded wait, a
+// failed check) leaves the outputs undefined, and the discarded weight becomes NaN
+__global__ void raw_status_kernel(const char* err_word, double* disc) {
+  if (*reinterpret_cast<const volatile int*>(err_word) != DEV_OK) *disc = __longlong_as_double(0x7ff8000000000000ll);
+}
+
 constexpr int kNoallocDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoallocDevices] = {};
@@ -1633,6 +1645,14 @@ int mps_kernel_stats_reset(mps_t h) {
 }
 
 // ---- raw-pointer two-site call
+int mps_debug_raw_wait(int barrier_extra, double timeout_s) {
+  if (barrier_extra < 0 || timeout_s < 0) return MPS_E_ARG;
+  g_raw_barrier_extra.store(barrier_extra, std::memory_order_relaxed);
+  g_raw_timeout_ns.store(timeout_s > 0 ? (unsigned long long)(timeout_s * 1e9) : kRawTimeoutNs,
+                         std::memory_order_relaxed);
+  return MPS_OK;
+}
+
 int mps_two_site_workspace(int precision, int chi_l, int chi_m, int chi_r, int chi_max, size_t* bytes) {
   if (!bytes || chi_l < 1 || chi_m < 1 || chi_r < 1 || chi_max < 1) return MPS_E_ARG;
   if (precision != MPS_PREC_FP64 && precision != MPS_PREC_MIXED) return MPS_E_ARG;
@@ -1664,8 +1684,8 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
   kn.nb = kDefaultNb;
   kn.G = std::min(num_sms(), kMaxCoop);
   kn.flag_tol = precision == MPS_PREC_FP64 ? 1.4901161193847656e-08 : 1e-3;
-  kn.timeout_ns = 10000000000ull;
-  kn.barrier_extra = 0;
+  kn.timeout_ns = g_raw_timeout_ns.load(std::memory_order_relaxed);
+  kn.barrier_extra = (unsigned)g_raw_barrier_extra.load(std::memory_order_relaxed);
   kn.use_tc = false;
   double* slot = discarded_dev ? discarded_dev : (double*)(base + L.disc);
   cudaError_t e;
@@ -1681,7 +1701,11 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
                            (const c64*)B, gt, (c64*)A_out, (c64*)B_out, slot, nullptr, s, nullptr);
   }
   (void)k;
-  return e == cudaSuccess ? MPS_OK : MPS_E_CUDA;
+  if (e != cudaSuccess) return MPS_E_CUDA;
+  // the call has no handle whose state could carry a device-side failure: a
+  // NaN discarded weight reports it, stream-ordered after the split
+  raw_status_kernel<<<1, 1, 0, s>>>(base + L.err, slot);
+  return cudaGetLastError() == cudaSuccess ? MPS_OK : MPS_E_CUDA;
 }
 
 int mps_two_site_apply_noalloc(int precision, int chi_l, int chi_m, int chi_r, int chi_max, const void* A,

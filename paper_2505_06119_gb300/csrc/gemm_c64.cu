@@ -356,10 +356,14 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
 
 template <int BM, bool THETA, bool BETA>
 cudaError_t launch(const GemmDesc<c64>& d, const ThetaEpi& te, dim3 grid, cudaStream_t s) {
-  // set once per instantiation; a function-local static is initialised thread-safely
-  static const cudaError_t attr = cudaFuncSetAttribute(gemm_c64_kernel<BM, THETA, BETA>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       g_smem_bytes<BM>());
+  // the attribute is set once per device and instantiation
+  static PerDevice once;
+  cudaError_t attr = cudaSuccess;
+  once.get([&attr]() -> long long {
+    attr = cudaFuncSetAttribute(gemm_c64_kernel<BM, THETA, BETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                g_smem_bytes<BM>());
+    return attr == cudaSuccess ? 1 : -1;
+  });
   if (attr != cudaSuccess) return attr;
   gemm_c64_kernel<BM, THETA, BETA><<<grid, G_NT, g_smem_bytes<BM>(), s>>>(d, te);
   return cudaGetLastError();

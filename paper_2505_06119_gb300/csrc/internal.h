@@ -3,11 +3,39 @@
 
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <atomic>
 #include <stdint.h>
 
 #include "common.cuh"
 
 namespace mpsg {
+
+// ---------------------------------------------------------------------------
+// First-use state kept per device ordinal (kernel attributes, occupancy, SM
+// counts).  A CUDA function attribute is set per device, so a process that
+// works on two devices needs one entry per device.  Entries are atomics: two
+// threads that fill the same entry at once both compute it and store the same
+// value, so no caller ever sees a half-made or default entry.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+  std::atomic<long long> v[kMaxDevices];  // value + 1; 0 = not computed yet
+  // The cached value for the current device, or compute() if there is none.
+  // compute() returns a value >= 0, or a negative code that is not cached.
+  template <typename F>
+  long long get(F compute) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return compute();
+    long long c = v[dev].load(std::memory_order_acquire);
+    if (c > 0) return c - 1;
+    const long long r = compute();
+    if (r >= 0) v[dev].store(r + 1, std::memory_order_release);
+    return r;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Generic complex GEMM on the CUDA cores:  C = alpha * opA * opB + beta * C.

@@ -1236,18 +1236,20 @@ __global__ void iota_kernel(int* p, int n) {
   if (i < n) p[i] = i;
 }
 
-int g_sms = 0;
+PerDevice g_sms;  // zero-initialised (static storage)
 
 }  // namespace
 
 int num_sms() {
-  if (g_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
-  }
-  return g_sms;
+  return (int)g_sms.get([]() -> long long {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 1;  // not cached: the next call asks again
+    }
+    return std::max(n, 1);
+  });
 }
 
 constexpr int kPanelSmem = 200 * 1024;  // dynamic shared memory of the panel kernel
@@ -1259,52 +1261,54 @@ constexpr int kCPanelSmem = 200 * 1024;
 // be resident, else 8, else 0 = not available).
 template <typename T>
 static int cpanel_cluster_size() {
-  static int cached = -1;
-  if (cached >= 0) return cached;
-  cached = 0;
-  if (cudaFuncSetAttribute(qr_cpanel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCPanelSmem) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return cached;
-  }
-  cudaFuncSetAttribute(qr_cpanel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaGetLastError();
-  for (int cs : {16, 8}) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(CPT);
-    cfg.dynamicSmemBytes = kCPanelSmem;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, qr_cpanel_kernel<T>, &cfg) == cudaSuccess && n >= 1) {
-      cached = cs;
-      break;
+  static PerDevice cache;
+  return (int)cache.get([]() -> long long {
+    if (cudaFuncSetAttribute(qr_cpanel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCPanelSmem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
     }
+    cudaFuncSetAttribute(qr_cpanel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
-  }
-  return cached;
+    for (int cs : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(CPT);
+      cfg.dynamicSmemBytes = kCPanelSmem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, qr_cpanel_kernel<T>, &cfg) == cudaSuccess && n >= 1) return cs;
+      cudaGetLastError();
+    }
+    return 0;
+  });
 }
 
 template <typename T>
 static cudaError_t panel_setup(int& max_blocks) {
-  static int cached = -1;
-  if (cached < 0) {
+  static PerDevice cache;
+  cudaError_t err = cudaSuccess;
+  const long long r = cache.get([&err]() -> long long {
     int smem = kPanelSmem;
-    cudaError_t e = cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+    err = cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return -1;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_panel_kernel<T>, PNT, smem);
-    if (e != cudaSuccess) return e;
-    cached = per_sm * num_sms();
-    if (cached < 1) return cudaErrorInvalidConfiguration;
-  }
-  max_blocks = cached;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_panel_kernel<T>, PNT, smem);
+    if (err != cudaSuccess) return -1;
+    if (per_sm * num_sms() < 1) {
+      err = cudaErrorInvalidConfiguration;
+      return -1;
+    }
+    return per_sm * num_sms();
+  });
+  if (r < 0) return err != cudaSuccess ? err : cudaErrorInvalidConfiguration;
+  max_blocks = (int)r;
   return cudaSuccess;
 }
 

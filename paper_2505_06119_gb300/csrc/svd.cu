@@ -332,27 +332,24 @@ __global__ void svd_right_kernel(const T* X, int64_t ldx, const int* perm, int M
 }
 
 // launch shape of the Jacobi kernel for `pairs` pairs per round: warps per CTA so
-// that the pairs spread over every SM, CTAs capped by co-residency
-// (the co-residency per block size is cached in atomics: handles on different
-// threads may fill an entry at the same time, with the same value)
+// that the pairs spread over every SM, CTAs capped by co-residency (cached per
+// device and block size)
 template <typename T>
 void jacobi_shape(int pairs, int& G, int& warps) {
-  static std::atomic<int> cap[2][kJMaxWarps + 1];
+  static PerDevice cap[2][kJMaxWarps + 1];
   const int sms = num_sms();
   warps = std::max(1, std::min(kJMaxWarps, (pairs + sms - 1) / sms));
-  std::atomic<int>& slot = cap[sizeof(T) == 8 ? 0 : 1][warps];
-  int c = slot.load(std::memory_order_relaxed);
-  if (c == 0) {
+  const int w = warps;
+  const long long c = cap[sizeof(T) == 8 ? 0 : 1][warps].get([w, sms]() -> long long {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, 32 * warps, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, 32 * w, 0) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
     }
-    c = per_sm * sms;
-    slot.store(c, std::memory_order_relaxed);
-  }
-  G = std::max(1, std::min(c, (pairs + warps - 1) / warps));
+    return (long long)per_sm * sms;
+  });
+  G = std::max(1, std::min((int)c, (pairs + warps - 1) / warps));
 }
 
 }  // namespace

@@ -344,15 +344,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   (void)ok;
 }
 
-bool g_tc_init = false;
+PerDevice g_tc_init;  // kernel attribute set once per device
 
 cudaError_t tc_setup() {
-  if (!g_tc_init) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    g_tc_init = true;
-  }
-  return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  g_tc_init.get([&e]() -> long long {
+    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    return e == cudaSuccess ? 1 : -1;
+  });
+  return e;
 }
 
 TcOperand operand_a(const GemmDesc<c64>& d) {

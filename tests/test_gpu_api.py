@@ -142,3 +142,99 @@ def test_launch_accounting_and_profile():
         assert st["panel"]["ms"] > 0
         m.kernel_stats_reset()
         assert m.kernel_stats()["panel"]["launches"] == 0
+
+
+@pytest.mark.parametrize("noalloc", [False, True])
+def test_raw_call_reports_expired_wait_as_nan(noalloc):
+    """The raw-pointer calls have no handle: a bounded wait that expires shows as a
+    NaN discarded weight; with the normal limits restored the next call is finite
+    and correct (the error word and barrier words are cleared per call)."""
+    import torch
+
+    from paper_2505_06119_gb300 import _lib as L
+    from paper_2505_06119_gb300.mps import _gate
+
+    lib = L.load()
+    rng = np.random.default_rng(5)
+    cl, cm, cr, chi = 24, 16, 20, 32
+    a = states.complex_gaussian(rng, (cl, 2, cm))
+    b = states.complex_gaussian(rng, (cm, 2, cr))
+    g = gates.haar_unitary(rng, 4)
+    dev = torch.device("cuda:0")
+    ta = torch.from_numpy(a).to(dev)
+    tb = torch.from_numpy(b).to(dev)
+    k = min(2 * cl, 2 * cr, chi)
+    sz = ctypes.c_size_t()
+    assert lib.mps_two_site_workspace(L.MPS_PREC_FP64, cl, cm, cr, chi, ctypes.byref(sz)) == 0
+    ws = torch.empty(sz.value + 256, dtype=torch.uint8, device=dev)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        oa = torch.empty((cl, 2, k), dtype=torch.complex128, device=dev)
+        ob = torch.empty((k, 2, cr), dtype=torch.complex128, device=dev)
+        disc = torch.zeros(1, dtype=torch.float64, device=dev)
+        if noalloc:
+            rc = lib.mps_two_site_apply_noalloc(L.MPS_PREC_FP64, cl, cm, cr, chi, ta.data_ptr(), tb.data_ptr(),
+                                                _gate(g, 16), oa.data_ptr(), ob.data_ptr(), disc.data_ptr(), stream)
+        else:
+            rc = lib.mps_two_site_apply(L.MPS_PREC_FP64, cl, cm, cr, chi, ta.data_ptr(), tb.data_ptr(),
+                                        _gate(g, 16), oa.data_ptr(), ob.data_ptr(), disc.data_ptr(), base,
+                                        sz.value, stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        return disc.item(), ob.cpu().numpy()
+
+    assert lib.mps_debug_raw_wait(-1, 0.0) == L.MPS_E_ARG
+    assert lib.mps_debug_raw_wait(1, 0.05) == 0
+    try:
+        d_bad, _ = call()
+    finally:
+        assert lib.mps_debug_raw_wait(0, 0.0) == 0
+    assert np.isnan(d_bad)
+    d_ok, ob = call()
+    assert np.isfinite(d_ok) and d_ok > 0
+    # kept norm + discarded weight = ||theta||^2 = ||A B||^2 (the gate is unitary)
+    x = np.einsum("lcm,mdr->lcdr", a, b)
+    assert d_ok + np.linalg.norm(ob) ** 2 == pytest.approx(np.linalg.norm(x) ** 2, rel=1e-10)
+
+
+@pytest.mark.skipif("not __import__('torch').cuda.is_available() or __import__('torch').cuda.device_count() < 2",
+                    reason="needs two visible GPUs")
+def test_handles_and_raw_calls_on_two_devices():
+    """First-use state (kernel attributes, occupancy) is kept per device: a handle on
+    device 1 after one on device 0, and raw calls on both, all work."""
+    import torch
+
+    from paper_2505_06119_gb300 import MPS, _lib as L
+    from paper_2505_06119_gb300.mps import _gate
+
+    rng = np.random.default_rng(8)
+    g = gates.haar_unitary(rng, 4)
+    res = []
+    for dev in (0, 1):
+        with MPS(12, 64, precision="mixed", device=dev) as m:
+            for i in range(11):
+                m.apply_2q(i, g)
+            m.move_centre(0)
+            res.append(m.fidelity())
+    assert res[0] == pytest.approx(res[1], rel=1e-6)
+    lib = L.load()
+    cl = cm = cr = chi = 48
+    a = states.complex_gaussian(rng, (cl, 2, cm)).astype(np.complex64)
+    b = states.complex_gaussian(rng, (cm, 2, cr)).astype(np.complex64)
+    outs = []
+    for dev in (0, 1):
+        with torch.cuda.device(dev):
+            d = torch.device("cuda:%d" % dev)
+            ta, tb = torch.from_numpy(a).to(d), torch.from_numpy(b).to(d)
+            oa = torch.empty((cl, 2, chi), dtype=torch.complex64, device=d)
+            ob = torch.empty((chi, 2, cr), dtype=torch.complex64, device=d)
+            disc = torch.zeros(1, dtype=torch.float64, device=d)
+            rc = lib.mps_two_site_apply_noalloc(L.MPS_PREC_MIXED, cl, cm, cr, chi, ta.data_ptr(), tb.data_ptr(),
+                                                _gate(g, 16), oa.data_ptr(), ob.data_ptr(), disc.data_ptr(),
+                                                torch.cuda.current_stream().cuda_stream)
+            assert rc == 0
+            torch.cuda.synchronize()
+            outs.append(ob.cpu().numpy())
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * np.abs(outs[0]).max()

@@ -84,3 +84,38 @@ def test_noalloc_rejects_oversized_problem(env):
     g = (L.mps_c128 * 16)()
     rc = lib.mps_two_site_apply_noalloc(L.MPS_PREC_FP64, 1024, 1024, 1024, 1024, 1, 1, g, 1, 1, None, None)
     assert rc == L.MPS_E_UNSUPPORTED
+
+
+def test_noalloc_allocates_no_device_memory(env):
+    """After a first call on the device (which looks up the array's address),
+    further calls leave the device's free memory and PyTorch's allocation count
+    unchanged: every byte of scratch comes from the library's fixed array."""
+    torch, L, lib = env
+    from paper_2505_06119_gb300.mps import _gate
+
+    rng = np.random.default_rng(12)
+    dev = torch.device("cuda:0")
+    cl, cm, cr, chi = 40, 32, 36, 48
+    k = min(2 * cl, 2 * cr, chi)
+    ta = torch.from_numpy(states.complex_gaussian(rng, (cl, 2, cm)).astype(np.complex64)).to(dev)
+    tb = torch.from_numpy(states.complex_gaussian(rng, (cm, 2, cr)).astype(np.complex64)).to(dev)
+    oa = torch.empty((cl, 2, k), dtype=torch.complex64, device=dev)
+    ob = torch.empty((k, 2, cr), dtype=torch.complex64, device=dev)
+    disc = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = _gate(gates.haar_unitary(rng, 4), 16)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        rc = lib.mps_two_site_apply_noalloc(L.MPS_PREC_MIXED, cl, cm, cr, chi, ta.data_ptr(), tb.data_ptr(), g,
+                                            oa.data_ptr(), ob.data_ptr(), disc.data_ptr(), stream)
+        assert rc == 0
+
+    call()
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info(0)[0], torch.cuda.memory_allocated(0)
+    for _ in range(5):
+        call()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(0)[0] == free0
+    assert torch.cuda.memory_allocated(0) == alloc0
+    assert np.isfinite(disc.item())
