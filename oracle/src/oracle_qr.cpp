@@ -25,6 +25,13 @@
 // With pivot = 0 steps 1-3 are skipped (plain QR, used to move the
 // orthogonality centre, Sec. III-C.1).
 //
+// oracle_cpqr_replay runs the same steps with the pivot of every step given
+// instead of chosen, and reports the chosen and the largest exact residual norm
+// of each step.  The paper leaves ties between equal column norms open; with
+// the replay a test can check that a pivot sequence chosen by another
+// implementation is greedy at every step and compare its factors with those of
+// that same sequence.
+//
 // Q[:, :k] = H_0 H_1 ... H_{k-1} I[:, :k] is formed by applying the reflectors
 // one at a time from the last to the first.
 //
@@ -66,22 +73,14 @@ double col_norm2(const cd* A, int64_t lda, int m, int r0, int t) {
   return s;
 }
 
-}  // namespace
-
-extern "C" {
-
-// Truncated (column-pivoted) Householder QR, in place.
-//   A     : m x n column-major, lda >= m; overwritten as described above.
-//   tau   : out, k entries.
-//   jpvt  : out, n entries; jpvt[t] = original index of the column now at t.
-//   k_out : out, number of reflectors k = min(m, n, kmax).
-//   discarded : out, ||A[k:m, k:n]||_F^2 after the k steps.
-// Returns 0, or -1 on a bad argument.
-int oracle_cpqr(int m, int n, int kmax, int pivot, void* A_, int64_t lda, void* tau_, int* jpvt,
-                int* k_out, double* discarded) {
+// The factorisation of oracle_cpqr.  With `order` given (pivot mode only), step
+// 2 takes the column whose original index is order[j] instead of the argmax and
+// records its exact squared norm in chosen2[j] and the step's largest one in
+// max2[j]: a replay of a pivot sequence chosen elsewhere.  Every other operation
+// is the same as without `order`.
+int cpqr_impl(int m, int n, int kmax, int pivot, cd* A, int64_t lda, cd* tau, int* jpvt, int* k_out,
+              double* discarded, const int* order, double* chosen2, double* max2) {
   if (m < 0 || n < 0 || kmax < 0 || lda < (m > 1 ? m : 1)) return -1;
-  cd* A = static_cast<cd*>(A_);
-  cd* tau = static_cast<cd*>(tau_);
   int k = m < n ? m : n;
   if (kmax < k) k = kmax;
   for (int t = 0; t < n; ++t) jpvt[t] = t;
@@ -95,6 +94,14 @@ int oracle_cpqr(int m, int n, int kmax, int pivot, void* A_, int64_t lda, void* 
       int p = j;
       for (int t = j + 1; t < n; ++t)
         if (c[t] > c[p]) p = t;
+      if (order) {  // replay: the given column, wherever it is now
+        max2[j] = c[p];
+        p = -1;
+        for (int t = j; t < n; ++t)
+          if (jpvt[t] == order[j]) p = t;
+        if (p < 0) return -1;  // order[j] is not among the remaining columns
+        chosen2[j] = c[p];
+      }
       // 3. swap columns j and p
       if (p != j) {
         cd* a = A + (int64_t)j * lda;
@@ -145,6 +152,36 @@ int oracle_cpqr(int m, int n, int kmax, int pivot, void* A_, int64_t lda, void* 
   *k_out = k;
   *discarded = disc;
   return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Truncated (column-pivoted) Householder QR, in place.
+//   A     : m x n column-major, lda >= m; overwritten as described above.
+//   tau   : out, k entries.
+//   jpvt  : out, n entries; jpvt[t] = original index of the column now at t.
+//   k_out : out, number of reflectors k = min(m, n, kmax).
+//   discarded : out, ||A[k:m, k:n]||_F^2 after the k steps.
+// Returns 0, or -1 on a bad argument.
+int oracle_cpqr(int m, int n, int kmax, int pivot, void* A_, int64_t lda, void* tau_, int* jpvt,
+                int* k_out, double* discarded) {
+  return cpqr_impl(m, n, kmax, pivot, static_cast<cd*>(A_), lda, static_cast<cd*>(tau_), jpvt, k_out, discarded,
+                   nullptr, nullptr, nullptr);
+}
+
+// The pivoted factorisation of oracle_cpqr with the pivot sequence given:
+// order[j] (j < k) is the original index of the column taken at step j.  Writes
+// what oracle_cpqr writes, plus chosen2[j] = exact squared residual norm of that
+// column at step j and max2[j] = the largest one over all remaining columns, so
+// a caller can check that every step took a greedy maximum (within a tolerance
+// when several columns tie).  Returns -1 if order[j] is out of range or repeats.
+int oracle_cpqr_replay(int m, int n, int kmax, const int* order, void* A_, int64_t lda, void* tau_, int* jpvt,
+                       int* k_out, double* discarded, double* chosen2, double* max2) {
+  if (!order || !chosen2 || !max2) return -1;
+  return cpqr_impl(m, n, kmax, 1, static_cast<cd*>(A_), lda, static_cast<cd*>(tau_), jpvt, k_out, discarded, order,
+                   chosen2, max2);
 }
 
 // Q[:, :k] = H_0 ... H_{k-1} I[:, :k] from the reflectors left in A by

@@ -156,3 +156,53 @@ def test_real_reflector_convention():
     f = qr.factor(a)
     assert f["w"][0, 0] == pytest.approx(-2.0)
     assert abs(f["tau"][0]) > 0
+
+
+# ---- pivot-sequence replay (checks of another implementation's pivot choices)
+
+def test_replay_of_own_order_reproduces_factorisation():
+    """Replaying the oracle's own pivots gives the same factors bit for bit, and every
+    step's chosen norm is the step's largest."""
+    rng = np.random.default_rng(41)
+    a = cgauss(rng, 50, 37)
+    q, r, p, disc = qr.cpqr(a, kmax=20)
+    q2, r2, p2, disc2, c2, m2 = qr.cpqr_replay(a, p[:20], kmax=20)
+    assert np.array_equal(p, p2)
+    assert np.array_equal(q, q2) and np.array_equal(r, r2) and disc == disc2
+    assert np.array_equal(c2, m2)
+
+
+@pytest.mark.parametrize("m,n,k", [(12, 9, 9), (30, 40, 17), (64, 48, 48)])
+def test_replay_with_any_order_is_the_qr_of_the_reordered_matrix(m, n, k):
+    """With an arbitrary pivot order the replay is the unpivoted Householder QR of the
+    chosen columns (LAPACK zgeqrf through NumPy, same reflector convention), R P^T = Q^H A
+    on every column, and the per-step norms equal brute-force projections."""
+    rng = np.random.default_rng(m + n + k)
+    a = cgauss(rng, m, n)
+    order = rng.permutation(n)[:k]
+    q, r, p, disc, c2, m2 = qr.cpqr_replay(a, order, kmax=k)
+    assert np.array_equal(p[:k], order)
+    qn, rn = np.linalg.qr(a[:, order])
+    assert np.abs(q - qn[:, :k]).max() < 1e-12 * m
+    assert np.abs(r[:, :k] - rn[:k, :k]).max() < 1e-12 * m
+    assert np.abs(q.conj().T @ a[:, p] - r).max() < 1e-12 * m
+    for j in range(k):
+        proj = a - qn[:, :j] @ (qn[:, :j].conj().T @ a)
+        res = np.sum(np.abs(proj) ** 2, axis=0)
+        rest = [t for t in range(n) if t not in set(order[:j].tolist())]
+        assert c2[j] == pytest.approx(res[order[j]], rel=1e-10, abs=1e-13)
+        assert m2[j] == pytest.approx(res[rest].max(), rel=1e-10, abs=1e-13)
+    kept = q @ r
+    assert disc == pytest.approx(np.sum(np.abs(a[:, p] - kept) ** 2), rel=1e-10)
+
+
+def test_replay_flags_a_non_greedy_step():
+    rng = np.random.default_rng(43)
+    a = cgauss(rng, 20, 16)
+    _, _, p, _ = qr.cpqr(a)
+    bad = p.copy()
+    bad[0], bad[1] = p[1], p[0]  # second-largest norm first
+    *_, c2, m2 = qr.cpqr_replay(a, bad)
+    assert c2[0] < m2[0]
+    with pytest.raises(ValueError):
+        qr.cpqr_replay(a, np.zeros(16, dtype=int))  # column 0 twice
