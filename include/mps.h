@@ -249,6 +249,17 @@ int mps_discarded_weight(mps_t h, double* total, long long* count);
  * split.  MPS_E_STATE on a QRCP handle.  Synchronous. */
 int mps_svd_last_stats(mps_t h, int* sweeps, long long* rotations);
 
+/* Column order of the most recent two-site split by pivoted QR that
+ * mps_apply_2q, mps_swap or mps_apply_2q_routed made on this handle
+ * (Sec. III-B.2, theta P = Q R): jpvt[t] for t < n is the column of theta,
+ * numbered b*chi_r + r for column (b, r), at pivot position t; the first k are
+ * the kept pivots in the order they were taken.  *n_out = n = 2 chi_r and
+ * *k_out = k of that split.  MPS_E_STATE when the workspace has been used for
+ * anything else since (a centre move, a layer, an MPO, an SVD split) or no
+ * such split was made; MPS_E_ARG when cap < n.  Synchronous.  A diagnostic: it
+ * lets a test check each pivot choice against an independent factorisation. */
+int mps_last_split_pivots(mps_t h, int* jpvt, int cap, int* n_out, int* k_out);
+
 /* Use `stream` (a cudaStream_t) for all further work; NULL = the handle's own. */
 int mps_set_stream(mps_t h, void* stream);
 /* Wait for all queued work; surfaces device-side errors. */

@@ -100,6 +100,7 @@ SIGNATURES = {
     "mps_two_site_apply_noalloc": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.POINTER(mps_c128), _P, _P,
                                         _P, _P]),
     "mps_debug_raw_wait": (_I, [_I, ctypes.c_double]),
+    "mps_last_split_pivots": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 
 _lib = None

@@ -427,6 +427,9 @@ struct mps_s {
   c128* d_E = nullptr;
   size_t E_elems = 0;
   long long nsplit = 0;
+  // shape of the last pivoted split whose pivots are still in the workspace
+  // (0 = the workspace was used for something else since)
+  int piv_n = 0, piv_k = 0;
   // layer path (lazy)
   std::vector<Lane> lanes;
   cudaEvent_t ev_fork = nullptr;
@@ -528,6 +531,7 @@ template <typename T>
 int move_right(mps_t h, int j) {
   using R = typename real_of<T>::type;
   Ws<T> w = views<T>(h);
+  h->piv_n = 0;
   const int cl = h->bond[j], cr = h->bond[j + 1], cn = h->bond[j + 2];
   const int m = 2 * cl, n = cr, k = std::min(m, n);
   T* sj = (T*)h->site[j];
@@ -576,6 +580,7 @@ template <typename T>
 int move_left(mps_t h, int j) {
   using R = typename real_of<T>::type;
   Ws<T> w = views<T>(h);
+  h->piv_n = 0;
   const int cp = h->bond[j - 1], cl = h->bond[j], cr = h->bond[j + 1];
   const int m = 2 * cr, n = cl, k = std::min(m, n);
   T* sj = (T*)h->site[j];
@@ -650,6 +655,7 @@ int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
   const int k = std::min(std::min(2 * cl, 2 * cr), chi);
   double* slot = h->d_disclog + (h->nsplit % kDiscLog);
   cudaError_t e;
+  h->piv_n = 0;
   if (h->trunc == MPS_TRUNC_SVD)
     e = two_site_svd<T>(w, h->svd_ws, h->SL, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1],
                         gt, (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
@@ -657,6 +663,10 @@ int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
     e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
                          (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
   if (e != cudaSuccess) return cuda_fail(h, e, "apply_2q");
+  if (h->trunc != MPS_TRUNC_SVD) {
+    h->piv_n = 2 * cr;
+    h->piv_k = k;
+  }
   h->bond[i + 1] = k;
   h->nsplit++;
   if (h->policy == MPS_POLICY_CANON) h->centre = i + 1;
@@ -694,6 +704,7 @@ int apply_mpo_t(mps_t h, int first, int count, const int* bonds, const mps_c128*
     if (rc) return rc;
   }
   Ws<T> w = views<T>(h);
+  h->piv_n = 0;
   LaunchHooks* hk = &h->prof.hooks;
   T* Y = (T*)h->mpo_ws;
   T* C = (T*)(h->mpo_ws + h->mpo_half);
@@ -828,6 +839,7 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
   }
   int rc = lanes_ready(h);
   if (rc) return rc;
+  h->piv_n = 0;
   struct Item {
     int j, cl, cm, cr, k;
     double work;
@@ -1622,6 +1634,22 @@ int mps_svd_last_stats(mps_t h, int* sweeps, long long* rotations) {
   for (int j = 0; j < std::min(std::max(sw, 0), kSvdMaxSweeps); ++j) tot += rot[j];
   *sweeps = sw;
   *rotations = tot;
+  return MPS_OK;
+}
+
+int mps_last_split_pivots(mps_t h, int* jpvt, int cap, int* n_out, int* k_out) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!jpvt || !n_out || !k_out) return fail(h, MPS_E_ARG, "last_split_pivots: null output");
+  if (h->piv_n <= 0) return fail(h, MPS_E_STATE, "last_split_pivots: no pivoted split in the workspace");
+  if (cap < h->piv_n) return fail(h, MPS_E_ARG, "last_split_pivots: capacity below the column count");
+  CUTRY(h, cudaMemcpyAsync(jpvt, views<c64>(h).jpvt, sizeof(int) * (size_t)h->piv_n, cudaMemcpyDeviceToHost,
+                           h->stream),
+        "last_split_pivots");
+  rc = check_device_error(h);
+  if (rc) return rc;
+  *n_out = h->piv_n;
+  *k_out = h->piv_k;
   return MPS_OK;
 }
 

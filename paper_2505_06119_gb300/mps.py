@@ -207,6 +207,17 @@ class MPS:
         self._check(self.lib.mps_svd_last_stats(self.h, ctypes.byref(sw), ctypes.byref(rot)))
         return sw.value, rot.value
 
+    def last_pivots(self):
+        """(jpvt, k) of the most recent pivoted two-site split: jpvt[t] is the theta
+        column (b * chi_r + r) at pivot position t; the first k were kept."""
+        b = self.bond_dims()
+        cap = 2 * max(b) + 2
+        arr = (ctypes.c_int * cap)()
+        n = ctypes.c_int()
+        k = ctypes.c_int()
+        self._check(self.lib.mps_last_split_pivots(self.h, arr, cap, ctypes.byref(n), ctypes.byref(k)))
+        return np.array(arr[:n.value], dtype=np.int64), k.value
+
     def sync(self):
         self._check(self.lib.mps_sync(self.h))
 

@@ -296,3 +296,45 @@ def test_embedding_change_swap_counts():
     m = omps.OracleMPS(rows * cols, 16, "canon")
     m.run(circuits.brickwall(rows * cols, 3, seed=1))
     assert m.permute(order) == circuits.inversions(order) == 15
+
+
+def test_paper_gate_set_produces_exact_pivot_ties():
+    """The random-circuit gate set of App. A (sqrt X / sqrt Y / sqrt W with fSim
+    couplers) makes tied column norms common: on a truncated 3 x 4 grid circuit the
+    oracle's own splits meet pivot steps whose two largest residual norms (brute-force
+    projections) agree to 1e-12.  This is why the GPU's splits of such circuits are
+    checked for greedy validity rather than for the oracle's tie-break."""
+    from oracle import qr as oqr
+
+    ops = circuits.grid_rcs(3, 4, 8, seed=11, singles="paper")
+    ref = omps.OracleMPS(12, 8, "canon")
+    ties = 0
+    for op in ops:
+        if op[0] == "1q":
+            ref.apply_1q(op[1], op[2])
+            continue
+        q1, q2, g = op[1], op[2], np.asarray(op[3])
+        if q1 > q2:
+            q1, q2, g = q2, q1, omps.SWAP @ g @ omps.SWAP
+        seq = [(b, omps.SWAP) for b in range(q1, q2 - 1)] + [(q2 - 1, g)]
+        seq += [(b, omps.SWAP) for b in range(q2 - 2, q1 - 1, -1)]
+        for i, gg in seq:
+            ref.move_centre(i)
+            a, b = ref.sites[i], ref.sites[i + 1]
+            cl, cm, cr = a.shape[0], a.shape[2], b.shape[2]
+            x = (a.reshape(2 * cl, cm) @ b.reshape(cm, 2 * cr)).reshape(cl, 2, 2, cr)
+            theta = np.einsum("abcd,lcdr->labr", gg.reshape(2, 2, 2, 2), x).reshape(2 * cl, 2 * cr)
+            _, _, p, _ = oqr.cpqr(theta, kmax=8)
+            k = min(theta.shape[0], theta.shape[1], 8)
+            for j in range(k):
+                if j:
+                    q = np.linalg.qr(theta[:, p[:j]])[0]
+                    res = np.sum(np.abs(theta - q @ (q.conj().T @ theta)) ** 2, axis=0)
+                else:
+                    res = np.sum(np.abs(theta) ** 2, axis=0)
+                res[p[:j]] = -1.0
+                top = np.sort(res)[::-1]
+                if len(top) > j + 1 and top[0] > 1e-20 and top[0] - top[1] <= 1e-12 * top[0]:
+                    ties += 1
+            ref.apply_2q(i, gg)
+    assert ties > 0
