@@ -220,7 +220,8 @@ def ours(args):
     achieved = panel["alg_bytes"] / (panel["ms"] * 1e-3) / 1e9 if panel["ms"] > 0 else 0.0
     m.close()
 
-    ms_step64 = f64 = fmx = dev_f = dev_o = None
+    ms_step64 = None
+    fid = {}
     if args.fp64_steps > 0:
         # --- FP64 path on the same steps
         m64 = MPS(n, chi, precision="fp64", policy="canon", stream=sptr, device=local)
@@ -228,22 +229,13 @@ def ours(args):
         ms64, st64 = time_steps_at(m64, seq, args.fp64_warmup, args.fp64_steps, torch, stream, i)
         ms_step64 = ms64 / args.fp64_steps
 
-        # --- fidelity deviation: a mixed state run through exactly the FP64 steps
+        # --- deviation of the mixed path from the FP64 path: a mixed state run through
+        # exactly the FP64 steps, compared result by result
         mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
         mm.set_sites([s.astype(np.complex64) for s in sites], centre=i)
         for stp in seq[:args.fp64_warmup + args.fp64_steps]:
             do_step_at(mm, stp, i)
-        f64 = m64.fidelity()
-        fmx = mm.fidelity()
-        dev_f = abs(fmx - f64) / f64
-    if args.fp64_steps > 0 and not args.skip_overlap:
-        # state-fidelity deviation 1 - |<mix|fp64>|^2 / (<mix|mix> <fp64|fp64>), all by
-        # full FP64 transfer-matrix contraction
-        o = mm.overlap(m64)
-        nmx = mm.overlap(mm).real
-        n64 = m64.overlap(m64).real
-        dev_o = 1.0 - abs(o) ** 2 / (nmx * n64)
-    if args.fp64_steps > 0:
+        fid = fidelity_deviation(mm, m64, n, i, args, np)
         mm.close()
         m64.close()
 
@@ -273,20 +265,16 @@ def ours(args):
         "vs_baseline": None,
         "dtype": "c64",
         "data": "synthetic",
-        "config": {
-            "workload": "steady-state two-site apply on a saturated bond, chi_l=chi_m=chi_r=%d, n=%d, "
-                        "canonical policy (centre move + 1q gates + gate/SWAP alternating per step)" % (chi, n),
-            "chi": chi, "n_sites": n, "bond_site": i, "policy": "canon",
-            "precision": "complex64 bulk, FP64 column norms / reflector norms / pivots",
-            "l2": "inputs larger than L2 (theta %d MiB)" % (((2 * chi) ** 2 * 8) >> 20),
-            "parallelism": "replicas" if ws > 1 else "single GPU",
-        },
+        "config": bench_config(chi, n, i, ws),
         "fp64_path": {"value": ws * 1e3 / ms_step64 if ms_step64 else None, "unit": "applies/s",
                       "ms_per_step": ms_step64, "steps": args.fp64_steps, "warmup": args.fp64_warmup,
                       "dtype": "c128"},
         "speedup_vs_fp64": ms_step64 / ms_step if ms_step64 else None,
-        "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o,
-                         "steps": args.fp64_warmup + args.fp64_steps, "f_fp64": f64, "f_mixed": fmx},
+        "tflops": FLOP_PER_APPLY * chi ** 3 * value / 1e12,
+        "tensor_roofline": tensor_roofline(FLOP_PER_APPLY * chi ** 3 * value / 1e12, peaks, peak_src,
+                                           FLOP_PER_APPLY * chi ** 3 * ws * 1e3 / ms_step64 / 1e12
+                                           if ms_step64 else None),
+        "fidelity_dev": fid,
         "roofline": {"bound": "hbm", "kernel": "qr_panel_kernel (pivoted-QR panel: per-step trailing GEMV)",
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / peaks.get("hbm_gbs", 1.0),
@@ -304,6 +292,69 @@ def ours(args):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# algorithmic real flops of one full-bond two-site apply per chi^3: theta contraction
+# 32, truncated pivoted QR 37.3, Q formation 13.3
+FLOP_PER_APPLY = 82.7
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 rate (nominal; no FP64 peak is measured on this machine)
+TF32_PER_BF16 = 0.5         # dense TF32 tensor rate relative to BF16 (nominal ratio 1.1 / 2.25 PF)
+
+
+def tensor_roofline(tflops_mixed, peaks, peak_src, tflops_fp64):
+    """Algorithmic TFLOP/s of the whole step as a fraction of the dense tensor rates:
+    BF16 (the measured sustained cuBLAS rate, the step being seconds long), TF32 (that
+    rate times the nominal TF32/BF16 ratio), and for the FP64 path the nominal FP64 rate."""
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0
+    out = {"tflops_mixed": tflops_mixed, "peak_bf16_tflops": bf16, "frac_bf16": tflops_mixed / bf16,
+           "peak_tf32_tflops": bf16 * TF32_PER_BF16, "frac_tf32": tflops_mixed / (bf16 * TF32_PER_BF16),
+           "peak_source": peak_src + " (bf16 sustained; tf32 = bf16 x 0.5 nominal ratio)"}
+    if tflops_fp64:
+        out.update({"tflops_fp64": tflops_fp64, "peak_fp64_tflops": FP64_NOMINAL_TFLOPS,
+                    "frac_fp64": tflops_fp64 / FP64_NOMINAL_TFLOPS, "fp64_peak_source": "nominal"})
+    return out
+
+
+def fidelity_deviation(mm, m64, n, i, args, np):
+    """Error of the mixed path against the FP64 path (which matches the FP64 oracle to
+    1e-10) after the same steps, per result: the norm fidelity (relative), the state
+    fidelity 1 - |<mix|64>|^2 / (<mix|mix><64|64>) (FP64 transfer matrices), sampled
+    amplitudes (absolute and relative to the largest sampled FP64 amplitude) and the
+    diagonal of R of the last split, |R_tt| for the kept pivots t < k (relative)."""
+    f64 = m64.fidelity()
+    fmx = mm.fidelity()
+    out = {"steps": args.fp64_warmup + args.fp64_steps, "f_fp64": f64, "f_mixed": fmx,
+           "norm_fidelity_rel": abs(fmx - f64) / f64,
+           "scope": "after the listed steps of this workload (a per-step bar); over the 390 truncating gates "
+                    "of the 40-qubit depth-20 brick-wall at chi 1024 the deviation is larger (about 2e-5), "
+                    "set by pivot decisions between residual norms closer than FP32 rounding"}
+    if not args.skip_overlap:
+        o = mm.overlap(m64)
+        nmx = mm.overlap(mm).real
+        n64 = m64.overlap(m64).real
+        out["overlap"] = 1.0 - abs(o) ** 2 / (nmx * n64)
+    rng = np.random.default_rng(2024)
+    amax = dmax = 0.0
+    for _ in range(args.amp_samples):
+        bits = rng.integers(0, 2, n)
+        a64 = m64.amplitude(bits)
+        dmax = max(dmax, abs(mm.amplitude(bits) - a64))
+        amax = max(amax, abs(a64))
+    out["amplitude_max_abs"] = dmax
+    out["amplitude_max_rel"] = dmax / amax if amax > 0 else None
+    out["amplitude_samples"] = args.amp_samples
+    # R diagonal of the last split: row t of the right site R P^T at column jpvt[t]
+    p64, k64 = m64.last_pivots()
+    pmx, kmx = mm.last_pivots()
+    r64 = m64.get_site(i + 1).reshape(k64, -1)
+    rmx = mm.get_site(i + 1).reshape(kmx, -1)
+    d64 = np.abs(r64[np.arange(k64), p64[:k64]])
+    dmx = np.abs(rmx[np.arange(kmx), pmx[:kmx]])
+    out["r_diag_rel_max"] = float(np.max(np.abs(dmx - d64) / np.maximum(d64, 1e-300)))
+    out["r_diag_rel_max_first_half"] = float(np.max(np.abs(dmx - d64)[:k64 // 2] / d64[:k64 // 2]))
+    out["pivots_equal"] = bool(np.array_equal(p64[:k64], pmx[:kmx]))
+    out["pivot_positions_differing"] = int(np.sum(p64[:k64] != pmx[:kmx]))
+    return out
 
 
 def replica_throughput(ms, e2e_seconds, steps, e2e_steps, ws, device="cuda"):
@@ -379,16 +430,18 @@ def e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np):
 
 
 # ---------------------------------------------------------------------------
-def oracle_apply_sample(chi_s, seed):
-    """One oracle step of the same recipe at bond chi_s: returns seconds."""
+def oracle_apply_sample(chi_s, seed, nsteps=2):
+    """nsteps oracle steps of the same recipe at bond chi_s (chi_s = 4096 is the
+    benchmark's own workload, n = 26): returns seconds per step."""
     from oracle import mps as omps
 
-    n = 2 * int(math.log2(chi_s)) + 2
+    n = N_SITES if chi_s == CHI else 2 * int(math.log2(chi_s)) + 2
     i = n // 2 - 1
     sites = make_state(chi_s, n, i, seed)
-    seq = step_gates(2, seed + 1)
+    seq = step_gates(nsteps, seed + 1)
     o = omps.OracleMPS(n, chi_s, "canon")
     o.set_sites(sites, centre=i)
+    del sites
     t0 = time.perf_counter()
     for st in seq:
         u1, u2, g = st
@@ -403,23 +456,39 @@ def oracle_apply_sample(chi_s, seed):
 
 def cpu_baseline(args, budget_s=None):
     """The oracle as it stands on this host's cores: a bounded sample of the same
-    step recipe at chi = 1024 (an apply at chi = 4096 takes minutes), scaled to the
-    chi = 4096 unit by the cubic work ratio (1024/4096)^3."""
+    step recipe at chi = 1024 (an apply at chi = 4096 takes about a minute), scaled to
+    the chi = 4096 unit by the cubic work ratio (1024/4096)^3."""
     from oracle import build as obuild
     from oracle import qr as oqr
 
     obuild.build()
     chi_s = args.cpu_chi
-    secs = oracle_apply_sample(chi_s, seed=7)
+    secs = oracle_apply_sample(chi_s, seed=7, nsteps=args.cpu_steps)
     scale = (chi_s / args.chi) ** 3
     return {"value": scale / secs, "unit": "applies/s", "cores": oqr.num_threads(), "kind": "oracle",
-            "sample": "2 oracle steps (same recipe: 1q gates, centre move, gate/SWAP, pivoted-QR split) at "
+            "sample": "%d oracle steps (same recipe: 1q gates, centre move, gate/SWAP, pivoted-QR split) at "
                       "chi=%d, %.2f s per step; applies/s scaled to chi=%d by (%d/%d)^3" % (
-                          chi_s, secs, args.chi, chi_s, args.chi),
+                          args.cpu_steps, chi_s, secs, args.chi, chi_s, args.chi),
             "seconds_per_sample_step": secs}
 
 
+def bench_config(chi, n, i, ws):
+    return {
+        "workload": "steady-state two-site apply on a saturated bond, chi_l=chi_m=chi_r=%d, n=%d, "
+                    "canonical policy (centre move + 1q gates + gate/SWAP alternating per step)" % (chi, n),
+        "chi": chi, "n_sites": n, "bond_site": i, "policy": "canon",
+        "precision": "complex64 bulk, FP64 column norms / reflector norms / pivots",
+        "l2": "inputs larger than L2 (theta %d MiB)" % (((2 * chi) ** 2 * 8) >> 20),
+        "parallelism": "replicas" if ws > 1 else "single GPU",
+    }
+
+
 def reference(args):
+    """The CPU oracle on this host's cores (the reference arm): W + K timed steps, each a
+    bounded sample of the workload (one oracle step of the same recipe at chi =
+    --cpu-chi; value = applies/s scaled to chi by the cubic work ratio), then, unless
+    --no-ref-full, one real oracle step at chi itself, reported beside it so that the
+    scaled value can be checked against a measured one."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
@@ -428,25 +497,74 @@ def reference(args):
 
     obuild.build()
     chi_s = args.cpu_chi
-    if args.warmup > 0:
-        oracle_apply_sample(chi_s, seed=3)
-    times = [oracle_apply_sample(chi_s, seed=11 + s) for s in range(max(1, args.steps))]
+    for w in range(args.warmup):
+        oracle_apply_sample(chi_s, seed=3 + w, nsteps=1)
+    times = [oracle_apply_sample(chi_s, seed=11 + s, nsteps=1) for s in range(max(1, args.steps))]
     secs = statistics.mean(times)
     scale = (chi_s / args.chi) ** 3
     value = scale / secs
+    full = None
+    if not args.no_ref_full:
+        fs = oracle_apply_sample(args.chi, seed=1234, nsteps=1)
+        full = {"chi": args.chi, "seconds": fs, "applies_per_s": 1.0 / fs,
+                "scaled_over_measured": value * fs}
+    n = N_SITES if args.chi == CHI else 2 * int(math.log2(args.chi)) + 2
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / scale,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
         "data": "synthetic",
-        "config": {"workload": "steady-state two-site apply on a saturated bond, chi_l=chi_m=chi_r=%d, "
-                               "canonical policy (CPU oracle)" % args.chi, "chi": args.chi},
+        "config": bench_config(args.chi, n, n // 2 - 1, ws),
+        "value_basis": "each timed step is one oracle step of the same recipe at chi=%d (ms_per_step is its "
+                       "wall time); value = applies/s at chi=%d by the cubic work ratio (%d/%d)^3" % (
+                           chi_s, args.chi, chi_s, args.chi),
+        "full_step_measured": full,
         "cpu_baseline": {"value": value, "unit": "applies/s", "cores": oqr.num_threads(), "kind": "oracle",
-                         "sample": "each step: 2 oracle steps of the same recipe at chi=%d, scaled to chi=%d "
-                                   "by (%d/%d)^3" % (chi_s, args.chi, chi_s, args.chi)},
+                         "sample": "each step: 1 oracle step of the same recipe at chi=%d, scaled to chi=%d "
+                                   "by (%d/%d)^3; plus one measured step at chi=%d" % (
+                                       chi_s, args.chi, chi_s, args.chi, args.chi)},
         "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def lapack_workload(args):
+    """The library CPU line: the same split through SciPy/LAPACK on this host's cores.
+    For each chi: theta = gate . (A B) (zgemm), then zgeqp3 (LAPACK's pivoted QR, which
+    has no truncation, so it factors the whole 2chi x 2chi theta) and zungqr for the kept
+    chi columns; seconds per apply, median of --lapack-reps."""
+    import numpy as np
+    import scipy.linalg.lapack as la
+
+    from workloads import gates, states
+
+    try:
+        blas = np.show_config(mode="dicts")["Build Dependencies"]["blas"]
+        blas = "%s %s" % (blas.get("name"), blas.get("version"))
+    except Exception:
+        blas = "unknown"
+    rows = []
+    for chi in [int(c) for c in args.lapack_chi.split(",")]:
+        rng = np.random.default_rng(chi)
+        a = states.complex_gaussian(rng, (chi, 2, chi))
+        b = states.complex_gaussian(rng, (chi, 2, chi))
+        g = gates.haar_unitary(rng, 4).reshape(2, 2, 2, 2)
+        ts = []
+        for _ in range(args.lapack_reps):
+            t0 = time.perf_counter()
+            x = (a.reshape(2 * chi, chi) @ b.reshape(chi, 2 * chi)).reshape(chi, 2, 2, chi)
+            theta = np.asfortranarray(np.einsum("abcd,lcdr->labr", g, x).reshape(2 * chi, 2 * chi))
+            lw = int(la.zgeqp3(theta, lwork=-1)[3][0].real)  # workspace query: the blocked QP3
+            qr_, jpvt, tau, work, info = la.zgeqp3(theta, lwork=max(lw, 1), overwrite_a=1)
+            lw2 = int(la.zungqr(qr_[:, :chi], tau[:chi], lwork=-1)[1][0].real)
+            q, work, info2 = la.zungqr(qr_[:, :chi], tau[:chi], lwork=max(lw2, 1))
+            ts.append(time.perf_counter() - t0)
+            assert info == 0 and info2 == 0
+        sec = statistics.median(ts)
+        rows.append({"chi": chi, "seconds_per_apply": sec, "applies_per_s": 1.0 / sec,
+                     "scaled_to_chi_%d" % CHI: (chi / CHI) ** 3 / sec})
+    print(json.dumps({"workload": "cpu-lapack", "blas": blas, "cores": os.cpu_count(),
+                      "steps": "zgemm + gate + zgeqp3 (full) + zungqr (k = chi)", "rows": rows}), flush=True)
 
 
 def layer_workload(args):
@@ -786,18 +904,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chi", type=int, default=CHI)
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=19)
+    ap.add_argument("--amp-samples", type=int, default=64)
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-chi", type=int, default=1024)
+    ap.add_argument("--cpu-steps", type=int, default=6)
+    ap.add_argument("--no-ref-full", action="store_true", help="reference arm: skip the real chi-sized step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-overlap", action="store_true")
-    ap.add_argument("--workload", default="gate", choices=["gate", "layer", "circuit", "big", "truncation", "iqft"],
+    ap.add_argument("--workload", default="gate",
+                    choices=["gate", "layer", "circuit", "big", "truncation", "iqft", "cpu-lapack"],
                     help="gate: the headline metric; layer: batched vs one-by-one layer times; "
                          "circuit: whole-circuit throughput and fidelity deviation; "
                          "big: one apply at a large bond dimension; "
                          "truncation: pivoted QR vs SVD splits (fidelity, runtime); "
-                         "iqft: random-saturation IQFT by controlled-phase MPOs")
+                         "iqft: random-saturation IQFT by controlled-phase MPOs; "
+                         "cpu-lapack: the split through SciPy/LAPACK on the host cores")
+    ap.add_argument("--lapack-chi", default="512,1024,2048")
+    ap.add_argument("--lapack-reps", type=int, default=2)
     ap.add_argument("--iqft-n", type=int, default=20)
     ap.add_argument("--iqft-chi", type=int, default=128)
     ap.add_argument("--iqft-sigma", default="0.125,0.25,0.5,1.0")
@@ -821,6 +946,8 @@ def main():
         truncation_workload(args)
     elif args.workload == "iqft":
         iqft_workload(args)
+    elif args.workload == "cpu-lapack":
+        lapack_workload(args)
     elif args.impl == "reference":
         reference(args)
     else:

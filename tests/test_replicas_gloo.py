@@ -74,10 +74,33 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
     monkeypatch.setenv("LOCAL_RANK", "1")
 
     class A:
-        steps, warmup, chi, cpu_chi = 1, 0, 4096, 1024
+        steps, warmup, chi, cpu_chi, no_ref_full = 1, 0, 4096, 1024, True
 
     assert bench.reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
+    """The reference arm's line: the oracle timed on small samples, the same config
+    as the GPU arm's line, and one real step at the line's own bond dimension."""
+    import json
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for k, v in (("RANK", "0"), ("WORLD_SIZE", "1"), ("LOCAL_RANK", "0")):
+        monkeypatch.setenv(k, v)
+
+    class A:
+        steps, warmup, chi, cpu_chi, no_ref_full = 2, 1, 64, 16, False
+
+    bench.reference(A())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2
+    assert line["config"] == bench.bench_config(64, 14, 6, 1)
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["full_step_measured"]["chi"] == 64 and line["full_step_measured"]["seconds"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
 
 
 FAIL_WORKER = r"""
