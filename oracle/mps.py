@@ -20,7 +20,10 @@ it.  Every step follows the paper's description:
   its squared norm is the norm fidelity of Sec. III-E.  With truncation="svd"
   the split is the truncated SVD instead (Sec. III-B.2 Table III, compared with
   pivoted QR in Sec. IV-A.1; oracle/svd.py): left site U[:, :k], right site
-  diag(S[:k]) V^dagger[:k, :], same k.
+  diag(S[:k]) V^dagger[:k, :], same k.  With truncation="rqrcp" the pivots are
+  chosen on a random sketch (oracle/rqrcp.py; one of the QR improvements the
+  bond-truncation discussion of Sec. IV-A.1 points to), the split is otherwise the
+  same; two-site split number s uses the sketch seed sketch_seed + s.
 * SWAP (Sec. III-C.4): the two-qubit path with the SWAP gate; a gate on
   non-adjacent positions lo < hi moves the qubit at lo rightwards by SWAPs on
   bonds (lo, lo+1) ... (hi-2, hi-1), applies the gate on (hi-1, hi), then
@@ -50,6 +53,7 @@ it.  Every step follows the paper's description:
 import numpy as np
 
 from . import qr as _qr
+from . import rqrcp as _rqrcp
 from . import svd as _svd
 
 
@@ -72,13 +76,14 @@ def physical_bond(n, b, chi):
 
 
 class OracleMPS:
-    def __init__(self, n, chi_max, policy="canon", truncation="qrcp"):
+    def __init__(self, n, chi_max, policy="canon", truncation="qrcp", sketch_seed=0):
         assert n >= 1 and chi_max >= 1 and policy in ("canon", "local")
-        assert truncation in ("qrcp", "svd")
+        assert truncation in ("qrcp", "svd", "rqrcp")
         self.n = n
         self.chi_max = chi_max
         self.policy = policy
         self.truncation = truncation
+        self.sketch_seed = sketch_seed  # rqrcp: split number s uses seed sketch_seed + s
         self.sites = []
         for _ in range(n):
             s = np.zeros((1, 2, 1), dtype=np.complex128)
@@ -100,7 +105,7 @@ class OracleMPS:
         self.centre = centre
 
     def copy(self):
-        o = OracleMPS(self.n, self.chi_max, self.policy, self.truncation)
+        o = OracleMPS(self.n, self.chi_max, self.policy, self.truncation, self.sketch_seed)
         o.sites = [s.copy() for s in self.sites]
         o.centre = self.centre
         o.discarded = list(self.discarded)
@@ -152,6 +157,11 @@ class OracleMPS:
         if self.truncation == "svd":
             q, right, _, disc = _svd.svd_split(theta, chi)
             k = q.shape[1]
+        elif self.truncation == "rqrcp":
+            res = _rqrcp.rqrcp(theta, chi, seed=self.sketch_seed + self.n_two_site)
+            q, k, disc = res["q"], res["k"], res["discarded"]
+            right = np.zeros((k, 2 * cr), dtype=np.complex128)
+            right[:, res["jpvt"]] = res["r"]
         else:
             q, r, jpvt, disc = _qr.cpqr(theta, kmax=chi, pivot=True)
             k = q.shape[1]
