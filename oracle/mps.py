@@ -258,6 +258,36 @@ class OracleMPS:
                     changed = True
         return swaps
 
+    def permute_layers(self, order, chi_max=None):
+        """The same site permutation by odd-even transposition sort, the parallel form of
+        the bubble sort above: pass t looks at the pairs (q, q+1) with q of the parity of
+        t, left to right, and swaps every pair whose target positions are out of order;
+        the SWAPs of one pass act on disjoint bonds, so they form one circuit layer.
+        Passes alternate until an even and an odd pass in a row find nothing to swap.
+        Returns (SWAPs, passes that swapped); the SWAP count is again the number of
+        inversions of the permutation."""
+        n = len(self.sites)
+        order = [int(x) for x in order]
+        assert sorted(order) == list(range(n)), "order must be a permutation of the positions"
+        dest = [0] * n
+        for p, q in enumerate(order):
+            dest[q] = p
+        swaps = passes = idle = 0
+        parity = 0
+        while idle < 2:
+            layer = []
+            for q in range(parity, n - 1, 2):
+                if dest[q] > dest[q + 1]:
+                    layer.append(q)
+                    dest[q], dest[q + 1] = dest[q + 1], dest[q]
+            for q in layer:
+                self.swap(q, chi_max)
+            swaps += len(layer)
+            passes += 1 if layer else 0
+            idle = 0 if layer else idle + 1
+            parity ^= 1
+        return swaps, passes
+
     def run(self, ops, chi_max=None):
         for op in ops:
             if op[0] == "1q":

@@ -338,3 +338,45 @@ def test_paper_gate_set_produces_exact_pivot_ties():
                     ties += 1
             ref.apply_2q(i, gg)
     assert ties > 0
+
+
+@pytest.mark.parametrize("policy", ["canon", "local"])
+def test_permute_layers_is_qubit_transposition_without_truncation(policy):
+    """Odd-even transposition sort of SWAPs without truncation: the statevector's axes
+    transposed, SWAP count = inversions (brute force), at most n passes, and (under the
+    local policy) the same state as the bubble-sort order."""
+    n = 7
+    rng = np.random.default_rng(43)
+    ops = circuits.brickwall(n, 4, seed=6)
+    for trial in range(4):
+        m = omps.OracleMPS(n, 128, policy)
+        m.run(ops)
+        v = m.statevector().reshape([2] * n)
+        order = list(rng.permutation(n)) if trial else list(range(n))[::-1]
+        swaps, passes = m.permute_layers(order)
+        inversions = sum(1 for a in range(n) for b in range(a + 1, n) if order[a] > order[b])
+        assert swaps == inversions and passes <= n
+        assert np.abs(m.statevector() - np.transpose(v, order).reshape(-1)).max() < 1e-12
+        if trial == 0:
+            assert passes == n  # the reversal needs n passes
+
+
+def test_permute_layers_passes_are_disjoint_layers():
+    """Each pass swaps pairs of one parity only, so the SWAPs of a pass act on disjoint
+    bonds (recorded by wrapping the oracle's swap)."""
+    n = 9
+    order = list(np.random.default_rng(3).permutation(n))
+    m = omps.OracleMPS(n, 4, "local")
+    seen = []
+    orig = m.swap
+    m.swap = lambda q, chi=None: (seen.append(q), orig(q, chi))
+    m.permute_layers(order)
+    # the recorded SWAPs split into runs of one parity, each strictly increasing by >= 2
+    i = 0
+    while i < len(seen):
+        par = seen[i] % 2
+        j = i
+        while j < len(seen) and seen[j] % 2 == par and (j == i or seen[j] > seen[j - 1]):
+            j += 1
+        assert all(b - a >= 2 for a, b in zip(seen[i:j], seen[i + 1:j]))
+        i = j
