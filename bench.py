@@ -205,7 +205,8 @@ def ours(args):
     sptr = stream.cuda_stream
 
     # --- mixed path, timed with per-kernel-class CUDA events
-    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, profile=True, device=local)
+    tr = {"truncation": args.truncation}
+    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, profile=True, device=local, **tr)
     m.set_sites([s.astype(np.complex64) for s in sites], centre=i)
     with ClockSampler(local) as clk:
         if ws > 1:
@@ -224,14 +225,14 @@ def ours(args):
     fid = {}
     if args.fp64_steps > 0:
         # --- FP64 path on the same steps
-        m64 = MPS(n, chi, precision="fp64", policy="canon", stream=sptr, device=local)
+        m64 = MPS(n, chi, precision="fp64", policy="canon", stream=sptr, device=local, **tr)
         m64.set_sites(sites, centre=i)
         ms64, st64 = time_steps_at(m64, seq, args.fp64_warmup, args.fp64_steps, torch, stream, i)
         ms_step64 = ms64 / args.fp64_steps
 
         # --- deviation of the mixed path from the FP64 path: a mixed state run through
         # exactly the FP64 steps, compared result by result
-        mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
+        mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local, **tr)
         mm.set_sites([s.astype(np.complex64) for s in sites], centre=i)
         for stp in seq[:args.fp64_warmup + args.fp64_steps]:
             do_step_at(mm, stp, i)
@@ -265,7 +266,7 @@ def ours(args):
         "vs_baseline": None,
         "dtype": "c64",
         "data": "synthetic",
-        "config": bench_config(chi, n, i, ws),
+        "config": bench_config(chi, n, i, ws, args.truncation),
         "fp64_path": {"value": ws * 1e3 / ms_step64 if ms_step64 else None, "unit": "applies/s",
                       "ms_per_step": ms_step64, "steps": args.fp64_steps, "warmup": args.fp64_warmup,
                       "dtype": "c128"},
@@ -403,7 +404,7 @@ def e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np):
     move, gate or SWAP, split) and reads the two new sites back."""
     from paper_2505_06119_gb300 import MPS
 
-    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local)
+    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local, truncation=args.truncation)
     m.set_sites([s.astype(np.complex64) for s in sites], centre=i)
     do_step(m, seq[0], i)
     shape_a = (chi, 2, chi)
@@ -472,12 +473,17 @@ def cpu_baseline(args, budget_s=None):
             "seconds_per_sample_step": secs}
 
 
-def bench_config(chi, n, i, ws):
+TRUNCATION_NAMES = {"qrcp": "truncated column-pivoted QR (QP3)",
+                    "rqrcp": "truncated QR with randomized column pivoting (RQRCP, sketch of 40 rows)"}
+
+
+def bench_config(chi, n, i, ws, truncation="qrcp"):
     return {
         "workload": "steady-state two-site apply on a saturated bond, chi_l=chi_m=chi_r=%d, n=%d, "
                     "canonical policy (centre move + 1q gates + gate/SWAP alternating per step)" % (chi, n),
         "chi": chi, "n_sites": n, "bond_site": i, "policy": "canon",
         "precision": "complex64 bulk, FP64 column norms / reflector norms / pivots",
+        "truncation": TRUNCATION_NAMES[truncation],
         "l2": "inputs larger than L2 (theta %d MiB)" % (((2 * chi) ** 2 * 8) >> 20),
         "parallelism": "replicas" if ws > 1 else "single GPU",
     }
@@ -906,6 +912,9 @@ def main():
     ap.add_argument("--chi", type=int, default=CHI)
     ap.add_argument("--fp64-steps", type=int, default=19)
     ap.add_argument("--amp-samples", type=int, default=64)
+    ap.add_argument("--truncation", default="qrcp", choices=["qrcp", "rqrcp"],
+                    help="split of the gate workload: the deterministic pivoted QR (the metric's) or "
+                         "randomized pivoting")
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-chi", type=int, default=1024)

@@ -83,6 +83,16 @@ extern "C" {
                             device memory, limits the handle to chi_max <= 4096, and is much slower
                             than QRCP: every sweep of the Jacobi iteration touches all column pairs. */
 
+#define MPS_TRUNC_RQRCP 2 /* truncated QR with randomized column pivoting (blocked RQRCP of Duersch-Gu and
+                            Martinsson et al.; one of the QR improvements Sec. IV-A.1 points to): the
+                            pivots of each block of panel-width columns come from a pivoted QR of a
+                            small random sketch Y = Omega theta (panel width + 8 rows, entries +-1
+                            from SplitMix64 with state sketch_seed + s for the s-th two-site split of
+                            the handle), the block itself is factored without pivoting and applied as
+                            one block reflector, and the sketch is updated as Y2 -= Y1 R11^{-1} R12.
+                            Pivots, and so the truncated state, differ from MPS_TRUNC_QRCP's; the
+                            kept rank and the norm identity are the same.  Layers run gate by gate. */
+
 /* host element formats for mps_get_site / mps_set_site */
 #define MPS_HOST_C128 0
 #define MPS_HOST_C64 1
@@ -123,8 +133,9 @@ typedef struct {
   int debug_max_ctas;     /* testing only, normally 0: caps the CTAs of the cooperative QR
                              panel kernel so that small matrices take the paths of large
                              ones (more than 128 rows per CTA); negative: MPS_E_ARG */
-  int truncation;         /* MPS_TRUNC_QRCP (default) or MPS_TRUNC_SVD */
-  int reserved[5];
+  int truncation;         /* MPS_TRUNC_QRCP (default), MPS_TRUNC_SVD or MPS_TRUNC_RQRCP */
+  int sketch_seed;        /* MPS_TRUNC_RQRCP: generator state of the first split's sketch (default 0) */
+  int reserved[4];
 } mps_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -170,6 +181,20 @@ int mps_apply_2q_routed(mps_t h, int q1, int q2, const mps_c128 g[16], int chi_m
  * Every SWAP truncates like a gate.  Host-side validation (MPS_E_ARG for a bad
  * order) happens before any SWAP; asynchronous otherwise. */
 int mps_permute(mps_t h, const int* order, int chi_max, long long* swaps);
+
+/* The site permutation of mps_permute as a pipeline of layers: odd-even
+ * transposition sort, the parallel form of that bubble sort (Sec. III-C site
+ * permutation; the re-embeddings of Sec. III-D.2).  Pass t takes the pairs
+ * (q, q+1) with q of the parity of t whose target positions are out of order;
+ * those SWAPs act on disjoint bonds and run as one mps_apply_layer call (its
+ * concurrent lanes).  Passes alternate until an even and an odd pass in a row
+ * find nothing to swap (at most n passes).  The SWAP count is again the number
+ * of inversions (*swaps), *passes the number of layers run (either may be
+ * NULL).  Requires MPS_POLICY_LOCAL (MPS_E_STATE otherwise); every SWAP
+ * truncates like a gate, so the state equals applying the passes' SWAPs one by
+ * one in pass order, which differs from mps_permute's order once truncation
+ * acts.  Host-side validation first; asynchronous otherwise. */
+int mps_permute_layers(mps_t h, const int* order, int chi_max, long long* swaps, int* passes);
 
 /* All two-qubit gates of one circuit layer, on pairwise disjoint bonds
  * sites[j], sites[j]+1 (gates[16*j .. 16*j+15]) (the gates of a brick-wall

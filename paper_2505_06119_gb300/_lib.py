@@ -24,6 +24,7 @@ MPS_POLICY_CANON = 0
 MPS_POLICY_LOCAL = 1
 MPS_TRUNC_QRCP = 0
 MPS_TRUNC_SVD = 1
+MPS_TRUNC_RQRCP = 2
 MPS_HOST_C128 = 0
 MPS_HOST_C64 = 1
 MPS_FLAG_PROFILE = 1
@@ -50,7 +51,7 @@ class mps_config(ctypes.Structure):
                 ("wait_timeout_s", ctypes.c_double), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("flags", ctypes.c_int),
                 ("debug_barrier_extra", ctypes.c_int), ("debug_max_ctas", ctypes.c_int),
-                ("truncation", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("truncation", ctypes.c_int), ("sketch_seed", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class mps_kstat(ctypes.Structure):
@@ -77,6 +78,8 @@ SIGNATURES = {
     "mps_apply_2q_routed": (_I, [_P, _I, _I, ctypes.POINTER(mps_c128), _I]),
     "mps_apply_layer": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(mps_c128), _I, _I]),
     "mps_permute": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_longlong)]),
+    "mps_permute_layers": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(_I)]),
     "mps_amplitude": (_I, [_P, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(mps_c128)]),
     "mps_fidelity_estimate": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
     "mps_overlap": (_I, [_P, _P, ctypes.POINTER(mps_c128)]),

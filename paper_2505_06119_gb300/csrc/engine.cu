@@ -236,14 +236,20 @@ cudaError_t theta_step(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, 
   return cudaSuccess;
 }
 
+struct SketchRef;
+template <typename T>
+void plan_sketch(QrPlan<T>& p, const SketchRef& sk);
+
+// sk != nullptr: the pivots are chosen on a random sketch (MPS_TRUNC_RQRCP)
 template <typename T>
 cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, int chi, const T* A, const T* B,
                           const T* g, T* Aout, T* Bout, double* disc_slot, double* disc_total, cudaStream_t s,
-                          LaunchHooks* hk) {
+                          LaunchHooks* hk, const SketchRef* sk = nullptr) {
   const int m = 2 * cl, n = 2 * cr;
   const int k = std::min(std::min(m, n), chi);
   CKE(theta_step<T>(w, kn, cl, cm, cr, A, B, g, s, hk));
   QrPlan<T> p = make_plan<T>(w, kn, m, n, k, 1, disc_slot, disc_total);
+  if (sk) plan_sketch<T>(p, *sk);
   CKE(qr_factor<T>(p, s, hk));
   CKE(qr_form_q<T>(p, w.Q, w.ldq, s, hk));
   hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * ((double)m * k + (double)k * n) * sizeof(T), 0);
@@ -280,6 +286,59 @@ SvdLayout svd_layout(size_t esz, int mmax) {
   L.fro2 = take(8);
   L.total = off;
   return L;
+}
+
+// scratch of the randomized-pivoting split (MPS_TRUNC_RQRCP), carved from one buffer
+struct SkLayout {
+  size_t Om, Ys, Yw, Ssk, tau, Wg, jpvt, seq, total;
+  int lsk = 0;
+  int64_t ldy = 0;
+};
+
+SkLayout sk_layout(size_t esz, int mmax, int nmax, int nb) {
+  SkLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  L.lsk = nb + kSketchOversample;
+  L.ldy = (L.lsk + 3) / 4 * 4;
+  const size_t mm = (size_t)std::max(mmax, 1), nn = (size_t)std::max(nmax, 1);
+  L.Om = take(esz * L.ldy * mm);
+  L.Ys = take(esz * L.ldy * nn);
+  L.Yw = take(esz * L.ldy * nn);
+  L.Ssk = take(esz * L.ldy * nb);
+  L.tau = take(esz * nb);
+  L.Wg = take(16 * (size_t)nb * nb);
+  L.jpvt = take(4 * nn);
+  L.seq = take(4 * (size_t)nb);
+  L.total = off;
+  return L;
+}
+
+// device pointers of that scratch for one split, with the sketch's generator state
+struct SketchRef {
+  char* base = nullptr;
+  const SkLayout* L = nullptr;
+  unsigned long long seed = 0;
+};
+
+template <typename T>
+void plan_sketch(QrPlan<T>& p, const SketchRef& sk) {
+  p.pivot = 2;
+  p.lsk = sk.L->lsk;
+  p.ldy = sk.L->ldy;
+  p.Om = (T*)(sk.base + sk.L->Om);
+  p.Ys = (T*)(sk.base + sk.L->Ys);
+  p.Yw = (T*)(sk.base + sk.L->Yw);
+  p.Ssk = (T*)(sk.base + sk.L->Ssk);
+  p.sk_tau = (T*)(sk.base + sk.L->tau);
+  p.sk_Wg = (c128*)(sk.base + sk.L->Wg);
+  p.sk_jpvt = (int*)(sk.base + sk.L->jpvt);
+  p.piv_seq = (int*)(sk.base + sk.L->seq);
+  p.seed = sk.seed;
 }
 
 // The two-site gate with the truncated SVD split (MPS_TRUNC_SVD): theta as in
@@ -417,6 +476,10 @@ struct mps_s {
   int trunc = MPS_TRUNC_QRCP;
   char* svd_ws = nullptr;
   SvdLayout SL;
+  // randomized-pivoting scratch (MPS_TRUNC_RQRCP only)
+  char* sk_ws = nullptr;
+  SkLayout SKL;
+  unsigned long long sketch_seed = 0;
   // FP64 observables scratch
   double* d_partial = nullptr;
   double* d_scalar = nullptr;  // [0] norm, [1] total discarded
@@ -659,7 +722,14 @@ int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
   if (h->trunc == MPS_TRUNC_SVD)
     e = two_site_svd<T>(w, h->svd_ws, h->SL, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1],
                         gt, (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
-  else
+  else if (h->trunc == MPS_TRUNC_RQRCP) {
+    SketchRef sk;
+    sk.base = h->sk_ws;
+    sk.L = &h->SKL;
+    sk.seed = h->sketch_seed + (unsigned long long)h->nsplit;  // split number s: seed + s
+    e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
+                         (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks, &sk);
+  } else
     e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
                          (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
   if (e != cudaSuccess) return cuda_fail(h, e, "apply_2q");
@@ -830,7 +900,7 @@ int lanes_ready(mps_t h) {
 template <typename T>
 int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi) {
   // per-class event timing needs one stream; the SVD split has one scratch per handle
-  if (h->prof.enabled || count <= 1 || h->trunc == MPS_TRUNC_SVD) {
+  if (h->prof.enabled || count <= 1 || h->trunc != MPS_TRUNC_QRCP) {
     for (int j = 0; j < count; ++j) {
       int rc = apply_2q_t<T>(h, sites[j], gates + 16 * j, chi);
       if (rc) return rc;
@@ -1209,7 +1279,8 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   if ((cfg.alloc == nullptr) != (cfg.free == nullptr)) return MPS_E_ARG;
   if (cfg.wait_timeout_s < 0) return MPS_E_ARG;
   if (cfg.debug_barrier_extra < 0 || cfg.debug_max_ctas < 0) return MPS_E_ARG;
-  if (cfg.truncation != MPS_TRUNC_QRCP && cfg.truncation != MPS_TRUNC_SVD) return MPS_E_ARG;
+  if (cfg.truncation != MPS_TRUNC_QRCP && cfg.truncation != MPS_TRUNC_SVD && cfg.truncation != MPS_TRUNC_RQRCP)
+    return MPS_E_ARG;
   if (cfg.truncation == MPS_TRUNC_SVD && chi_max > kSvdMaxChi) return MPS_E_UNSUPPORTED;
   mps_s* h = new (std::nothrow) mps_s();
   if (!h) return MPS_E_NOMEM;
@@ -1218,6 +1289,7 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   h->prec = cfg.precision;
   h->policy = cfg.policy;
   h->trunc = cfg.truncation;
+  h->sketch_seed = (unsigned long long)(unsigned)cfg.sketch_seed;
   h->device = cfg.device;
   h->ualloc = cfg.alloc;
   h->ufree = cfg.free;
@@ -1295,7 +1367,12 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
     h->SL = svd_layout(h->esz, 2 * chicap);
     h->svd_ws = (char*)dev_alloc(h, h->SL.total);
   }
-  if (!h->ws || !h->d_partial || !h->d_disclog || !h->d_vec || (h->trunc == MPS_TRUNC_SVD && !h->svd_ws)) {
+  if (h->trunc == MPS_TRUNC_RQRCP) {
+    h->SKL = sk_layout(h->esz, 2 * chicap, 2 * chicap, h->kn.nb);
+    h->sk_ws = (char*)dev_alloc(h, h->SKL.total);
+  }
+  if (!h->ws || !h->d_partial || !h->d_disclog || !h->d_vec || (h->trunc == MPS_TRUNC_SVD && !h->svd_ws) ||
+      (h->trunc == MPS_TRUNC_RQRCP && !h->sk_ws)) {
     release(h);
     delete h;
     return MPS_E_NOMEM;
@@ -1453,6 +1530,46 @@ int mps_permute(mps_t h, const int* order, int chi_max, long long* swaps) {
     }
   }
   if (swaps) *swaps = count;
+  return MPS_OK;
+}
+
+int mps_permute_layers(mps_t h, const int* order, int chi_max, long long* swaps, int* passes) {
+  int rc = usable(h);
+  if (rc) return rc;
+  if (!order) return fail(h, MPS_E_ARG, "permute_layers: null order");
+  if (chi_max > h->chi_max) return fail(h, MPS_E_ARG, "permute_layers: chi_max above the handle's");
+  if (h->policy != MPS_POLICY_LOCAL) return fail(h, MPS_E_STATE, "permute_layers: needs the local policy");
+  std::vector<int> dest(h->n, -1);  // dest[q] = final position of the site now at q
+  for (int p = 0; p < h->n; ++p) {
+    const int q = order[p];
+    if (q < 0 || q >= h->n || dest[q] >= 0) return fail(h, MPS_E_ARG, "permute_layers: order is not a permutation");
+    dest[q] = p;
+  }
+  long long count = 0;
+  int npass = 0;
+  std::vector<int> sites;
+  std::vector<mps_c128> gates;
+  for (int parity = 0, idle = 0; idle < 2; parity ^= 1) {
+    sites.clear();
+    for (int q = parity; q + 1 < h->n; q += 2)
+      if (dest[q] > dest[q + 1]) {
+        sites.push_back(q);
+        std::swap(dest[q], dest[q + 1]);
+      }
+    if (sites.empty()) {
+      ++idle;
+      continue;
+    }
+    idle = 0;
+    gates.resize(16 * sites.size());
+    for (size_t j = 0; j < sites.size(); ++j) memcpy(&gates[16 * j], swap_gate(), 16 * sizeof(mps_c128));
+    rc = mps_apply_layer(h, sites.data(), gates.data(), (int)sites.size(), chi_max);
+    if (rc) return rc;
+    count += (long long)sites.size();
+    ++npass;
+  }
+  if (swaps) *swaps = count;
+  if (passes) *passes = npass;
   return MPS_OK;
 }
 

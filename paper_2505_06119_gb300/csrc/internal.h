@@ -179,7 +179,23 @@ struct QrPlan {
   unsigned barrier_extra;  // 0 normally; >0 only to exercise the timeout path
   int kclass = -1;         // >= 0: attribute every launch to this kernel class
   bool use_tc = false;     // complex64 GEMMs on the tensor cores
+  // pivot == 2: pivots chosen on a random sketch (blocked randomized QRCP); the
+  // sketch scratch below is then required
+  int lsk = 0;              // sketch rows (nb + oversampling)
+  int64_t ldy = 0;          // leading dimension of Om, Ys, Yw, Ssk (>= lsk, multiple of 4)
+  T* Om = nullptr;          // ldy x m: sketching matrix (+-1)
+  T* Ys = nullptr;          // ldy x n: sketch, columns in the current order of W
+  T* Yw = nullptr;          // ldy x n: copy factored to choose one block's pivots
+  T* Ssk = nullptr;         // ldy x nb: Y_sel R11^{-1}
+  T* sk_tau = nullptr;      // nb: reflector scalars of the sketch panel
+  c128* sk_Wg = nullptr;    // nb x nb: w vectors of the sketch panel
+  int* sk_jpvt = nullptr;   // n: column order of the sketch panel
+  int* piv_seq = nullptr;   // nb: position taken at each step of the sketch panel
+  unsigned long long seed = 0;  // generator state of the sketching matrix
 };
+
+// sketch rows beyond the block size (oversampling) of the randomized QRCP
+constexpr int kSketchOversample = 8;
 
 struct LaunchHooks;  // profiling hooks (engine.cu)
 

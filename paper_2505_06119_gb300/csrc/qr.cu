@@ -85,6 +85,7 @@ struct PanelArgs {
   int xcap;    // elements of x that fit in dynamic shared memory
   int xs_off;  // byte offset of the x vector in dynamic shared memory
   int bulk;    // phase D streams column chunks with bulk asynchronous copies
+  int* piv_seq;  // optional: the pivot position p taken at each step
 };
 
 // Squared column norm below which a reflector is the identity (tau = 0): in
@@ -531,6 +532,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       a.jpvt[J] = a.jpvt[p];
       a.jpvt[p] = t0;
     }
+    if (b == 0 && tid == 0 && a.piv_seq) a.piv_seq[kk] = p;
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
 
     // ---------------- C: reflector (every CTA, identical FP64 arithmetic).
@@ -1436,6 +1438,75 @@ static cudaError_t apply_block(const QrPlan<T>& p, int j0, int kbb, const T* Tb,
   return gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s);
 }
 
+// Launch one panel (pivoted or not) described by `a` (every data field set):
+// chooses bulk copies, the grid size and the shared memory; an unpivoted panel
+// whose rows fit the shared memory of one cluster runs on qr_cpanel_kernel when
+// `cluster_ok`.
+template <typename T>
+static cudaError_t launch_panel(PanelArgs<T>& a, unsigned barrier_extra, int gcap, bool cluster_ok, cudaStream_t s) {
+  const int m = a.m, j0 = a.j0, kb = a.kb;
+  const int smem = kPanelSmem;
+  // bulk copies need 16-byte aligned column chunks: an aligned base, a
+  // 16-byte multiple column stride and (complex64) chunks of whole row pairs
+  a.bulk = (reinterpret_cast<uintptr_t>(a.W) % 16 == 0) && ((a.ldw * (int64_t)sizeof(T)) % 16 == 0) &&
+           (sizeof(T) == 16 || m % 2 == 0);
+  const int ncols = a.nend - j0;
+  // enough CTAs for both the per-step row work (phase B) and the trailing columns
+  int G = std::max(1, std::min(gcap, std::max((ncols + 7) / 8, (m - j0 + 63) / 64)));
+  a.expected = (unsigned)G + barrier_extra;
+  int dyn;
+  if (a.bulk) {
+    // bulk mode: the copy slots, then x when it fits beside them (else x is
+    // read from global memory, where it stays in L2)
+    const int64_t xb = ((int64_t)(m - j0 + 2) * sizeof(T) + 15) / 16 * 16;
+    const bool fits = kRing + xb <= smem;
+    dyn = kRing + (fits ? (int)xb : 0);
+    a.xs_off = kRing;
+    a.xcap = fits ? (int)(xb / (int64_t)sizeof(T)) : 0;
+  } else {
+    // dynamic shared memory sized to the x vector this panel stages (rounded
+    // to 16 KB): the rest of the SM's unified L1/shared storage stays L1,
+    // which holds the trailing sweep's loads in flight
+    const int need = (int)std::min<int64_t>((int64_t)(m - j0 + 2) * sizeof(T), smem);
+    dyn = std::min(smem, (need + 16383) / 16384 * 16384);
+    a.xs_off = 0;
+    a.xcap = dyn / (int)sizeof(T);
+  }
+  void* args[] = {&a};
+  // unpivoted panels whose rows fit the shared memory of one cluster run on it
+  const int ccs = (a.pivot || !cluster_ok) ? 0 : cpanel_cluster_size<T>();
+  const int crb = ccs > 0 ? ((m - j0 + ccs - 1) / ccs + 1) / 2 * 2 : 0;
+  if (ccs > 0 && (int64_t)kb * crb * (int64_t)sizeof(T) <= kCPanelSmem) {
+    CPanelArgs<T> ca;
+    ca.W = a.W;
+    ca.ldw = a.ldw;
+    ca.m = m;
+    ca.j0 = j0;
+    ca.kb = kb;
+    ca.nb = a.nb;
+    ca.rb = crb;
+    ca.tau = a.tau;
+    ca.Wg = a.Wg;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ccs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ccs);
+    cfg.blockDim = dim3(CPT);
+    cfg.dynamicSmemBytes = (size_t)kb * crb * sizeof(T);
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, qr_cpanel_kernel<T>, ca);
+  }
+  return cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<T>, dim3(G), dim3(PNT), args, (size_t)dyn, s);
+}
+
+template <typename T>
+cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks);
+
 template <typename T>
 cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
   using R = typename real_of<T>::type;
@@ -1456,6 +1527,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     }
     return cudaSuccess;
   }
+  if (p.pivot == 2) return qr_factor_sketched<T>(p, s, hooks);
   int maxb = 1;
   CK(panel_setup<T>(maxb));
   const int gcap = std::max(1, std::min(p.G > 0 ? p.G : maxb, maxb));
@@ -1472,7 +1544,6 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     CK(cudaGetLastError());
     hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
   }
-  const int smem = kPanelSmem;
   int tblk_done = 0;  // outer blocks whose factor the unpivoted trailing updates already built
   for (int pi = 0; pi < npanels; ++pi) {
     const int j0 = pi * nb;
@@ -1504,71 +1575,15 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     a.err = p.err;
     a.timeout_ns = p.timeout_ns;
     a.flag_tol = p.flag_tol;
-    // bulk copies need 16-byte aligned column chunks: an aligned base, a
-    // 16-byte multiple column stride and (complex64) chunks of whole row pairs
-    a.bulk = (reinterpret_cast<uintptr_t>(p.W) % 16 == 0) && ((p.ldw * (int64_t)sizeof(T)) % 16 == 0) &&
-             (sizeof(T) == 16 || m % 2 == 0);
-    const int ncols = a.nend - j0;
-    // enough CTAs for both the per-step row work (phase B) and the trailing columns
-    int G = std::max(1, std::min(gcap, std::max((ncols + 7) / 8, (m - j0 + 63) / 64)));
-    a.expected = (unsigned)G + p.barrier_extra;
-    // algorithmic bytes: per step one read of the trailing block rows J..m
+    a.piv_seq = nullptr;
     double bytes = 0.0, flops = 0.0;
-    for (int j = j0; j < J1; ++j) {
+    for (int j = j0; j < J1; ++j) {  // algorithmic: per step one read of the trailing block rows J..m
       double rows = (double)(m - j), cols = (double)(a.nend - j);
       bytes += rows * cols * sizeof(T);
       flops += 8.0 * rows * cols;
     }
-    int dyn;
-    if (a.bulk) {
-      // bulk mode: the copy slots, then x when it fits beside them (else x is
-      // read from global memory, where it stays in L2)
-      const int64_t xb = ((int64_t)(m - j0 + 2) * sizeof(T) + 15) / 16 * 16;
-      const bool fits = kRing + xb <= smem;
-      dyn = kRing + (fits ? (int)xb : 0);
-      a.xs_off = kRing;
-      a.xcap = fits ? (int)(xb / (int64_t)sizeof(T)) : 0;
-    } else {
-      // dynamic shared memory sized to the x vector this panel stages (rounded
-      // to 16 KB): the rest of the SM's unified L1/shared storage stays L1,
-      // which holds the trailing sweep's loads in flight
-      const int need = (int)std::min<int64_t>((int64_t)(m - j0 + 2) * sizeof(T), smem);
-      dyn = std::min(smem, (need + 16383) / 16384 * 16384);
-      a.xs_off = 0;
-      a.xcap = dyn / (int)sizeof(T);
-    }
-    void* args[] = {&a};
     hook_before(hooks, K(MPS_KCLASS_PANEL), bytes, flops);
-    // unpivoted panels whose rows fit the shared memory of one cluster run on it
-    const int ccs = p.pivot ? 0 : cpanel_cluster_size<T>();
-    const int crb = ccs > 0 ? ((m - j0 + ccs - 1) / ccs + 1) / 2 * 2 : 0;
-    if (ccs > 0 && (int64_t)kb * crb * (int64_t)sizeof(T) <= kCPanelSmem) {
-      CPanelArgs<T> ca;
-      ca.W = p.W;
-      ca.ldw = p.ldw;
-      ca.m = m;
-      ca.j0 = j0;
-      ca.kb = kb;
-      ca.nb = nb;
-      ca.rb = crb;
-      ca.tau = p.tau;
-      ca.Wg = a.Wg;
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = ccs;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(ccs);
-      cfg.blockDim = dim3(CPT);
-      cfg.dynamicSmemBytes = (size_t)kb * crb * sizeof(T);
-      cfg.stream = s;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      CK(cudaLaunchKernelEx(&cfg, qr_cpanel_kernel<T>, ca));
-    } else {
-      CK(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<T>, dim3(G), dim3(PNT), args, (size_t)dyn, s));
-    }
+    CK(launch_panel<T>(a, p.barrier_extra, gcap, !p.pivot, s));
     hook_after(hooks, K(MPS_KCLASS_PANEL), 1);
     if (p.pivot) {
       if (J1 < n && J1 < m) {
@@ -1650,6 +1665,273 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     discarded_kernel<<<1, 256, 0, s>>>(p.vn1, k, n, p.discarded, p.disc_total);
     CK(cudaGetLastError());
     hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Truncated QR with randomized column pivoting (pivot == 2): blocked RQRCP of
+// Duersch and Gu / Martinsson et al.  The pivots of each block of nb columns are
+// chosen by nb steps of the pivoted panel kernel on a small sketch Y = Omega W
+// (lsk = nb + oversampling rows) instead of on W itself; the block is then
+// factored without pivoting (the centre-move panel kernels) and applied to the
+// whole trailing matrix as one block reflector (GEMMs), and the sketch of the
+// trailing columns is updated as Y2 -= (Y1 R11^{-1}) R12.  The per-pivot pass
+// over the trailing matrix of QP3 is gone; what remains per pivot is the panel's
+// own column work and a pass over the short sketch.
+
+// Omega (ldy x m, column-major, rows < lsk): entry (i, r) = -1 when the top bit of
+// SplitMix64 output number i*m + r is set, else +1.  SplitMix64 (Steele, Lea and
+// Flood, OOPSLA 2014) as a counter-based generator: the output for counter c is
+// the mixing function applied to seed + (c + 1) * 0x9E3779B97F4A7C15 (mod 2^64).
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long c) {
+  unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void sketch_omega_kernel(T* Om, int64_t ldy, int lsk, int m, unsigned long long seed) {
+  using R = typename real_of<T>::type;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ldy * (int64_t)m) return;
+  const int i = (int)(idx % ldy);
+  const int64_t r = idx / ldy;
+  R v = 0;
+  if (i < lsk) v = (splitmix64_at(seed, (unsigned long long)i * (unsigned long long)m + (unsigned long long)r) >> 63)
+                       ? R(-1)
+                       : R(1);
+  Om[idx] = mk<R>(v, 0);
+}
+
+// The column swaps a sketch panel made, applied to another matrix: for t < kb, in
+// order, swap columns j0 + t and j0 + seq[t] of A (rows [0, rows)); with jpvt the
+// same swaps are made on jpvt (block 0).
+template <typename T>
+__global__ void apply_swaps_kernel(T* A, int64_t lda, int rows, int j0, const int* seq, int kb, int* jpvt) {
+  __shared__ int s_seq[kPanelNbMax];
+  if (threadIdx.x < kb) s_seq[threadIdx.x] = seq[threadIdx.x];
+  __syncthreads();
+  if (jpvt && blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int t = 0; t < kb; ++t) {
+      const int q = j0 + s_seq[t];
+      const int x = jpvt[j0 + t];
+      jpvt[j0 + t] = jpvt[q];
+      jpvt[q] = x;
+    }
+  }
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    for (int t = 0; t < kb; ++t) {
+      const int q = j0 + s_seq[t];
+      if (q == j0 + t) continue;
+      T* a = A + r + (int64_t)(j0 + t) * lda;
+      T* b = A + r + (int64_t)q * lda;
+      const T x = *a;
+      *a = *b;
+      *b = x;
+    }
+  }
+}
+
+// S (ldy x kb, rows < lsk) with S R11 = Y[:, j0:j0+kb], R11 = W[j0:j0+kb, j0:j0+kb]
+// upper triangular, by forward substitution per sketch row; a diagonal entry whose
+// squared modulus is below the smallest normal number of the data type (a column
+// with no residual) contributes nothing (its column of S is zero).
+template <typename T>
+__global__ void sketch_solve_kernel(const T* Ys, int64_t ldy, int lsk, int j0, int kb, const T* W, int64_t ldw,
+                                    T* S) {
+  using R = typename real_of<T>::type;
+  __shared__ T r11[kPanelNbMax][kPanelNbMax + 1];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int i = e % kb, j = e / kb;
+    r11[i][j] = i <= j ? W[j0 + i + (int64_t)(j0 + j) * ldw] : mk<R>(0, 0);
+  }
+  __syncthreads();
+  const double tiny = sizeof(R) == 8 ? 2.2250738585072014e-308 : 1.1754943508222875e-38;
+  for (int i = threadIdx.x; i < lsk; i += blockDim.x) {
+    T sv[kPanelNbMax];
+    for (int c = 0; c < kb; ++c) {
+      T rhs = Ys[i + (int64_t)(j0 + c) * ldy];
+      for (int t = 0; t < c; ++t) rhs = rhs - sv[t] * r11[t][c];
+      const T d = r11[c][c];
+      const double d2 = (double)d.re * (double)d.re + (double)d.im * (double)d.im;
+      T q = mk<R>(0, 0);
+      if (d2 >= tiny) {
+        const R inv = (R)(1.0 / d2);
+        q = rhs * mk<R>(d.re * inv, -d.im * inv);  // rhs / d
+      }
+      sv[c] = q;
+      S[i + (int64_t)c * ldy] = q;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
+  using R = typename real_of<T>::type;
+  const ClassMap K{p.kclass};
+  const int m = p.m, n = p.n, k = p.k, nb = p.nb, l = p.lsk;
+  const int64_t ldy = p.ldy;
+  if (!p.Om || !p.Ys || !p.Yw || !p.Ssk || !p.sk_tau || !p.sk_Wg || !p.sk_jpvt || !p.piv_seq || l < nb ||
+      ldy < l)
+    return cudaErrorInvalidValue;
+  int maxb = 1;
+  CK(panel_setup<T>(maxb));
+  const int gcap = std::max(1, std::min(p.G > 0 ? p.G : maxb, maxb));
+  // the sketch panel is short (l rows): a few CTAs keep its grid barriers cheap
+  const int gsk = std::max(1, std::min(gcap, 32));
+  const int npanels = (k + nb - 1) / nb;
+  CK(cudaMemsetAsync(p.Tfac, 0, sizeof(T) * (size_t)npanels * nb * nb, s));
+  // Y = Omega W
+  hook_before(hooks, K(MPS_KCLASS_OTHER), (double)m * n * sizeof(T), 8.0 * l * m * n);
+  iota_kernel<<<(n + 255) / 256, 256, 0, s>>>(p.jpvt, n);
+  CK(cudaGetLastError());
+  {
+    const int64_t tot = ldy * (int64_t)m;
+    sketch_omega_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p.Om, ldy, l, m, p.seed);
+    CK(cudaGetLastError());
+    GemmDesc<T> d;
+    d.M = l;
+    d.N = n;
+    d.K = m;
+    d.alpha = mk<R>(1, 0);
+    d.beta = mk<R>(0, 0);
+    d.A = p.Om;
+    d.lda = ldy;
+    d.a_row = 0;
+    d.B = p.W;
+    d.ldb = p.ldw;
+    d.b_row = 0;
+    d.C = p.Ys;
+    d.ldc = ldy;
+    d.splitk = choose_splitk(l, n, m, p.sk_cap, (int)sizeof(T));
+    d.wk = p.SK;
+    CK(gemm_simt<T>(d, s));
+    hook_after(hooks, K(MPS_KCLASS_OTHER), 2 + gemm_launches(d));
+  }
+  for (int pi = 0; pi < npanels; ++pi) {
+    const int j0 = pi * nb;
+    const int kb = std::min(nb, k - j0);
+    const int J1 = j0 + kb;
+    const int nr = n - j0;
+    // a. the block's pivots: kb steps of the pivoted panel on a copy of the sketch's
+    //    remaining columns, which records the position taken at each step
+    hook_before(hooks, K(MPS_KCLASS_PANEL), (double)l * nr * kb * sizeof(T), 8.0 * l * nr * kb);
+    CK(cudaMemcpyAsync(p.Yw, p.Ys + (int64_t)j0 * ldy, sizeof(T) * (size_t)ldy * nr, cudaMemcpyDeviceToDevice, s));
+    iota_kernel<<<(nr + 255) / 256, 256, 0, s>>>(p.sk_jpvt, nr);
+    CK(cudaGetLastError());
+    col_norms_kernel<T><<<(nr + 7) / 8, 256, 0, s>>>(p.Yw, ldy, l, 0, 0, nr, p.vn1, p.vn2);
+    CK(cudaGetLastError());
+    PanelArgs<T> a;
+    a.W = p.Yw;
+    a.ldw = ldy;
+    a.m = l;
+    a.n = nr;
+    a.j0 = 0;
+    a.kb = kb;
+    a.nend = nr;
+    a.nb = nb;
+    a.pivot = 1;
+    a.F = p.F;
+    a.vn1 = p.vn1;
+    a.vn2 = p.vn2;
+    a.jpvt = p.sk_jpvt;
+    a.tau = p.sk_tau;
+    a.Tp = nullptr;
+    a.Wg = p.sk_Wg;
+    a.red_norm = p.red_norm;
+    a.red_w = reinterpret_cast<T*>(p.red_w);
+    a.red_argv = reinterpret_cast<long long*>(p.red_argv);
+    a.red_argi = p.red_argi;
+    a.alpha_slot = p.alpha_slot;
+    a.bar = p.bar;
+    a.err = p.err;
+    a.timeout_ns = p.timeout_ns;
+    a.flag_tol = p.flag_tol;
+    a.piv_seq = p.piv_seq;
+    CK(launch_panel<T>(a, p.barrier_extra, gsk, false, s));
+    // the same column swaps on W, on the sketch and on jpvt
+    apply_swaps_kernel<T><<<std::max(1, std::min(1024, (m + 255) / 256)), 256, 0, s>>>(p.W, p.ldw, m, j0, p.piv_seq,
+                                                                                      kb, p.jpvt);
+    CK(cudaGetLastError());
+    apply_swaps_kernel<T><<<1, 256, 0, s>>>(p.Ys, ldy, l, j0, p.piv_seq, kb, nullptr);
+    CK(cudaGetLastError());
+    hook_after(hooks, K(MPS_KCLASS_PANEL), 5);
+    // b. the block without pivoting (as a centre move's panel)
+    PanelArgs<T> b = a;
+    b.W = p.W;
+    b.ldw = p.ldw;
+    b.m = m;
+    b.n = n;
+    b.j0 = j0;
+    b.nend = J1;
+    b.pivot = 0;
+    b.jpvt = p.jpvt;
+    b.tau = p.tau;
+    b.Tp = p.Tfac + (size_t)pi * nb * nb;
+    b.Wg = p.Wg + (size_t)pi * nb * nb;
+    b.piv_seq = nullptr;
+    double bytes = 0.0, flops = 0.0;
+    for (int j = j0; j < J1; ++j) {
+      bytes += (double)(m - j) * (J1 - j) * sizeof(T);
+      flops += 8.0 * (m - j) * (J1 - j);
+    }
+    hook_before(hooks, K(MPS_KCLASS_PANEL), bytes, flops);
+    CK(launch_panel<T>(b, p.barrier_extra, gcap, true, s));
+    hook_after(hooks, K(MPS_KCLASS_PANEL), 1);
+    if (J1 < n) {
+      // the block reflector on every column to the right (rows j0..m)
+      int nl = 1;
+      const double M = m - j0, N = n - J1;
+      hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * kb + 3.0 * M * N) * sizeof(T), 16.0 * M * N * kb);
+      tfactor_kernel<T><<<1, 1024, 0, s>>>(p.Wg, p.tau, pi, k, nb, p.Tfac);
+      CK(cudaGetLastError());
+      CK(apply_block<T>(p, j0, kb, p.Tfac + (size_t)pi * nb * nb, nb, 1, p.W, p.ldw, J1, n - J1, &nl, s));
+      hook_after(hooks, K(MPS_KCLASS_UPDATE), nl);
+      // c. sketch update Y[:, J1:] -= (Y[:, j0:J1] R11^{-1}) R12
+      hook_before(hooks, K(MPS_KCLASS_OTHER), (double)(l + kb) * N * sizeof(T) * 2, 8.0 * l * kb * N);
+      sketch_solve_kernel<T><<<1, 64, 0, s>>>(p.Ys, ldy, l, j0, kb, p.W, p.ldw, p.Ssk);
+      CK(cudaGetLastError());
+      GemmDesc<T> d;
+      d.M = l;
+      d.N = n - J1;
+      d.K = kb;
+      d.alpha = mk<R>(-1, 0);
+      d.beta = mk<R>(1, 0);
+      d.A = p.Ssk;
+      d.lda = ldy;
+      d.a_row = 0;
+      d.B = p.W + j0 + (int64_t)J1 * p.ldw;
+      d.ldb = p.ldw;
+      d.b_row = 0;
+      d.C = p.Ys + (int64_t)J1 * ldy;
+      d.ldc = ldy;
+      CK(gemm_simt<T>(d, s));
+      hook_after(hooks, K(MPS_KCLASS_OTHER), 2);
+    }
+  }
+  {
+    // triangular factors for Q formation: every panel's, then the outer blocks
+    int nl = 1;
+    hook_before(hooks, K(MPS_KCLASS_FORMQ), 0, 0);
+    tfactor_kernel<T><<<npanels, 1024, 0, s>>>(p.Wg, p.tau, 0, k, nb, p.Tfac);
+    CK(cudaGetLastError());
+    for (int pb = 0; pb < npanels; pb += 2) {
+      int kbb = 0;
+      CK(outer_tfactor<T>(p, pb, &kbb, &nl, s));
+    }
+    hook_after(hooks, K(MPS_KCLASS_FORMQ), nl);
+  }
+  if (p.discarded) {
+    // discarded = ||W[k:m, k:n]||_F^2
+    hook_before(hooks, K(MPS_KCLASS_NORMS), (double)std::max(0, m - k) * (n - k) * sizeof(T), 0);
+    if (k < n)
+      col_norms_kernel<T><<<(n - k + 7) / 8, 256, 0, s>>>(p.W, p.ldw, m, k, k, n, p.vn1, p.vn2);
+    CK(cudaGetLastError());
+    discarded_kernel<<<1, 256, 0, s>>>(p.vn1, k, n, p.discarded, p.disc_total);
+    CK(cudaGetLastError());
+    hook_after(hooks, K(MPS_KCLASS_NORMS), k < n ? 2 : 1);
   }
   return cudaSuccess;
 }

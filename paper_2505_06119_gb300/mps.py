@@ -30,7 +30,7 @@ def _gate(g, n):
 
 def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile=False,
            wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False, debug_max_ctas=0,
-           truncation="qrcp"):
+           truncation="qrcp", sketch_seed=0):
     lib = L.load()
     cfg = L.mps_config()
     lib.mps_config_init(ctypes.byref(cfg))
@@ -43,7 +43,8 @@ def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile
     cfg.device = device
     cfg.debug_barrier_extra = debug_barrier_extra
     cfg.debug_max_ctas = debug_max_ctas
-    cfg.truncation = {"qrcp": L.MPS_TRUNC_QRCP, "svd": L.MPS_TRUNC_SVD}[truncation]
+    cfg.truncation = {"qrcp": L.MPS_TRUNC_QRCP, "svd": L.MPS_TRUNC_SVD, "rqrcp": L.MPS_TRUNC_RQRCP}[truncation]
+    cfg.sketch_seed = sketch_seed
     return cfg
 
 
@@ -120,6 +121,15 @@ class MPS:
         cnt = ctypes.c_longlong()
         self._check(self.lib.mps_permute(self.h, o, chi_max, ctypes.byref(cnt)))
         return cnt.value
+
+    def permute_layers(self, order, chi_max=0):
+        """The same permutation by odd-even transposition sort, one layer of disjoint
+        SWAPs per pass (local policy).  Returns (SWAPs, passes)."""
+        o = (ctypes.c_int * max(len(order), 1))(*[int(x) for x in order])
+        cnt = ctypes.c_longlong()
+        npass = ctypes.c_int()
+        self._check(self.lib.mps_permute_layers(self.h, o, chi_max, ctypes.byref(cnt), ctypes.byref(npass)))
+        return cnt.value, npass.value
 
     def run(self, ops, chi_max=0):
         for op in ops:

@@ -87,7 +87,7 @@ def test_host_argument_checks(lib):
     assert lib.mps_create_ex(ctypes.byref(h), 4, 4, ctypes.byref(cfg)) == L.MPS_E_ARG
     lib.mps_config_init(ctypes.byref(cfg))
     assert cfg.truncation == L.MPS_TRUNC_QRCP
-    cfg.truncation = 2
+    cfg.truncation = 3  # unknown truncation mode
     assert lib.mps_create_ex(ctypes.byref(h), 4, 4, ctypes.byref(cfg)) == L.MPS_E_ARG
     cfg.truncation = L.MPS_TRUNC_SVD  # the SVD split is limited to chi_max <= 4096
     assert lib.mps_create_ex(ctypes.byref(h), 30, 8192, ctypes.byref(cfg)) == L.MPS_E_UNSUPPORTED

@@ -228,3 +228,44 @@ def test_apply_layer_matches_oracle_local_policy(n, depth, chi, prec):
             ov = abs(got.overlap(ref)) ** 2 / (got.norm2() * ref.norm2())
             assert ov >= 1 - 1e-4
     assert ref.norm2() < 0.999
+
+
+# ---------------------------------------------------------------------------
+# site permutation as a pipeline of SWAP layers
+
+@pytest.mark.parametrize("prec,n,chi", [("fp64", 12, 8), ("fp64", 20, 32), ("mixed", 20, 32)])
+def test_permute_layers_matches_oracle(prec, n, chi):
+    """mps_permute_layers (odd-even transposition sort, each pass one batched layer of
+    SWAPs) on a truncated random state against the oracle's permute_layers: SWAP and
+    pass counts, bond dims, and the state (FP64: norm fidelity 1e-9 and amplitudes
+    1e-10; mixed: state fidelity >= 1 - 1e-4)."""
+    ops = circuits.brickwall(n, 8, seed=17)
+    order = list(np.random.default_rng(n).permutation(n))
+    ref = omps.OracleMPS(n, chi, "local")
+    ref.run(ops)
+    sw_ref, ps_ref = ref.permute_layers(order)
+    with gpu_mps(n, chi, precision=prec, policy="local") as m:
+        m.run(ops)
+        sw, ps = m.permute_layers(order)
+        assert (sw, ps) == (sw_ref, ps_ref)
+        assert m.bond_dims() == ref.bond_dims()
+        if prec == "fp64":
+            assert m.fidelity() == pytest.approx(ref.norm2(), rel=1e-9)
+            rng = np.random.default_rng(5)
+            for _ in range(16):
+                bits = rng.integers(0, 2, n)
+                assert abs(m.amplitude(bits) - ref.amplitude(bits)) < 1e-10
+        else:
+            got = omps.OracleMPS(n, chi, "local")
+            got.set_sites([m.get_site(i) for i in range(n)])
+            assert abs(got.overlap(ref)) ** 2 / (got.norm2() * ref.norm2()) >= 1 - 1e-4
+    assert ref.norm2() < 0.9999
+
+
+def test_permute_layers_needs_local_policy():
+    from paper_2505_06119_gb300 import MPSError, _lib as L
+
+    with gpu_mps(6, 8, precision="fp64", policy="canon") as m:
+        with pytest.raises(MPSError) as ei:
+            m.permute_layers([1, 0, 2, 3, 4, 5])
+        assert ei.value.code == L.MPS_E_STATE
