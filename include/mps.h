@@ -99,6 +99,11 @@ extern "C" {
 
 /* mps_config.flags */
 #define MPS_FLAG_PROFILE 1          /* time the tracked kernels with CUDA events (mps_kernel_stats) */
+#define MPS_FLAG_AUTOTUNE 4         /* choose the QR panel width and the pivoted panel kernel's CTA count of
+                                       every two-site split shape (precision, 2 chi_l, 2 chi_r, k) by timing
+                                       the candidates on the first split of that shape (see
+                                       mps_tune_two_site); layers use the choice too.  Off by default: the
+                                       choice can change the rounding, though not the bars of the results. */
 #define MPS_FLAG_TENSOR_CORES 2     /* mixed precision: long-K complex products (theta, centre-move
                                        absorption) on the tcgen05 tensor cores with 3xTF32 splitting.
                                        Off by default: the tensor cores' FP32 accumulation drifts
@@ -338,6 +343,26 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
                        const void* A, const void* B, const mps_c128 g[16], void* A_out,
                        void* B_out, double* discarded_dev, void* workspace, size_t ws_bytes,
                        void* stream);
+
+/* Autotuner of the two-site split (the paper tunes its block size chi_b by a sweep,
+ * Sec. IV-A.3; here the knobs are GB300's): times one split of the shape
+ * (chi_l, chi_m, chi_r, chi_max) in the given precision on seeded random sites with
+ * every candidate QR panel width {32, 16, 8} x CTA count of the pivoted panel kernel
+ * {all, 3/4, 1/2 of the SMs} and keeps the fastest, in a process-wide cache keyed by
+ * (precision, 2 chi_l, 2 chi_r, k, SM count).  When the environment variable
+ * MPS_TUNE_CACHE names a file, the cache is first filled from it and every new
+ * entry is appended to it as one JSON object per line.  force = 0 returns a cached
+ * entry without timing (out->candidates = 0).  Handles created with
+ * MPS_FLAG_AUTOTUNE consult the same cache.  Allocates its own device memory on the
+ * current device and synchronises.  MPS_E_ARG for bad sizes, MPS_E_NOMEM, MPS_E_CUDA. */
+typedef struct {
+  int panel_width;   /* chosen QR panel width nb */
+  int panel_ctas;    /* chosen CTA count of the pivoted panel kernel */
+  int candidates;    /* configurations timed (0: taken from the cache) */
+  double ms;         /* one split with the chosen configuration (CUDA events, best of the runs) */
+  double default_ms; /* one split with the defaults (panel width 32, every SM) */
+} mps_tune_result;
+int mps_tune_two_site(int precision, int chi_l, int chi_m, int chi_r, int chi_max, int force, mps_tune_result* out);
 
 /* Testing only: every later raw-pointer call (mps_two_site_apply and
  * mps_two_site_apply_noalloc) bounds its device-side waits by timeout_s

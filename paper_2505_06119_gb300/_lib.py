@@ -29,6 +29,7 @@ MPS_HOST_C128 = 0
 MPS_HOST_C64 = 1
 MPS_FLAG_PROFILE = 1
 MPS_FLAG_TENSOR_CORES = 2
+MPS_FLAG_AUTOTUNE = 4
 MPS_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other", "canon", "svd"]
@@ -52,6 +53,11 @@ class mps_config(ctypes.Structure):
                 ("alloc_ctx", ctypes.c_void_p), ("flags", ctypes.c_int),
                 ("debug_barrier_extra", ctypes.c_int), ("debug_max_ctas", ctypes.c_int),
                 ("truncation", ctypes.c_int), ("sketch_seed", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class mps_tune_result(ctypes.Structure):
+    _fields_ = [("panel_width", ctypes.c_int), ("panel_ctas", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
 
 class mps_kstat(ctypes.Structure):
@@ -103,6 +109,7 @@ SIGNATURES = {
     "mps_two_site_apply_noalloc": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.POINTER(mps_c128), _P, _P,
                                         _P, _P]),
     "mps_debug_raw_wait": (_I, [_I, ctypes.c_double]),
+    "mps_tune_two_site": (_I, [_I, _I, _I, _I, _I, _I, ctypes.POINTER(mps_tune_result)]),
     "mps_last_split_pivots": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 

@@ -10,6 +10,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -496,6 +497,10 @@ struct mps_s {
   // layer path (lazy)
   std::vector<Lane> lanes;
   cudaEvent_t ev_fork = nullptr;
+  // autotuning (MPS_FLAG_AUTOTUNE): scratch outputs of the timed candidate splits
+  bool tune = false;
+  char* tune_ws = nullptr;
+  size_t tune_half = 0;
   // status
   int status = MPS_OK;
   std::string msg;
@@ -586,6 +591,197 @@ int usable(mps_t h) {
     return MPS_E_STATE;
   }
   if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, MPS_E_CUDA, "cudaSetDevice failed");
+  return MPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the two-site split.  Per (precision, m, n, k, SM count) the
+// candidates panel width nb in {32, 16, 8} x CTAs of the pivoted panel kernel in
+// {all, 3/4, 1/2 of the SMs} are timed on the problem itself (CUDA events, the
+// best of `reps` runs after one warm-up) and the fastest is kept.  The GEMM tiles
+// are not searched: the rank-nb and block-reflector products (K <= 64) always take
+// the 64-row tile and the theta contraction the 128-row one.  One process-wide
+// cache; when the environment variable MPS_TUNE_CACHE names a file, entries are
+// read from it at first use and appended to it, one JSON object per line.
+struct TuneEntry {
+  int prec = 0, m = 0, n = 0, k = 0, sms = 0;
+  int nb = 0, ctas = 0, candidates = 0;
+  double ms = 0, default_ms = 0;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+bool g_tune_loaded = false;
+
+bool json_num(const char* line, const char* key, double* v) {
+  char pat[64];
+  snprintf(pat, sizeof pat, "\"%s\":", key);
+  const char* q = strstr(line, pat);
+  if (!q) return false;
+  q += strlen(pat);
+  while (*q == ' ') ++q;
+  char* end = nullptr;
+  const double x = strtod(q, &end);
+  if (end == q) return false;
+  *v = x;
+  return true;
+}
+
+bool tune_parse(const char* line, TuneEntry* e) {
+  double v[10];
+  const char* keys[10] = {"m", "n", "k", "sms", "panel_width", "panel_ctas", "ms", "default_ms", "candidates",
+                          "complex_bytes"};
+  for (int i = 0; i < 10; ++i)
+    if (!json_num(line, keys[i], &v[i])) return false;
+  e->m = (int)v[0];
+  e->n = (int)v[1];
+  e->k = (int)v[2];
+  e->sms = (int)v[3];
+  e->nb = (int)v[4];
+  e->ctas = (int)v[5];
+  e->ms = v[6];
+  e->default_ms = v[7];
+  e->candidates = (int)v[8];
+  e->prec = v[9] == 16 ? MPS_PREC_FP64 : MPS_PREC_MIXED;
+  return e->nb >= 1 && e->nb <= kMaxNb && e->ctas >= 1;
+}
+
+TuneEntry* tune_find_locked(int prec, int m, int n, int k, int sms) {
+  if (!g_tune_loaded) {
+    g_tune_loaded = true;
+    const char* path = getenv("MPS_TUNE_CACHE");
+    if (path && *path) {
+      if (FILE* f = fopen(path, "r")) {
+        char line[512];
+        while (fgets(line, sizeof line, f)) {
+          TuneEntry e;
+          if (tune_parse(line, &e)) g_tune.push_back(e);  // a later line for the same key wins
+        }
+        fclose(f);
+      }
+    }
+  }
+  TuneEntry* hit = nullptr;
+  for (TuneEntry& e : g_tune)
+    if (e.prec == prec && e.m == m && e.n == n && e.k == k && e.sms == sms) hit = &e;
+  return hit;
+}
+
+void tune_store_locked(const TuneEntry& e) {
+  g_tune.push_back(e);
+  const char* path = getenv("MPS_TUNE_CACHE");
+  if (!path || !*path) return;
+  if (FILE* f = fopen(path, "a")) {
+    fprintf(f,
+            "{\"precision\": \"%s\", \"complex_bytes\": %d, \"m\": %d, \"n\": %d, \"k\": %d, \"sms\": %d, "
+            "\"panel_width\": %d, \"panel_ctas\": %d, \"ms\": %.6g, \"default_ms\": %.6g, \"candidates\": %d}\n",
+            e.prec == MPS_PREC_FP64 ? "c128" : "c64", e.prec == MPS_PREC_FP64 ? 16 : 8, e.m, e.n, e.k, e.sms, e.nb,
+            e.ctas, e.ms, e.default_ms, e.candidates);
+    fclose(f);
+  }
+}
+
+// Time the candidates on one split: A, B inputs (read only), Aout, Bout and
+// *disc scratch outputs; w a workspace laid out for nb = kMaxNb and base.G CTAs.
+template <typename T>
+cudaError_t tune_split(const Ws<T>& w, const Knobs& base, int cl, int cm, int cr, int chi, const T* A, const T* B,
+                       const T* g, T* Aout, T* Bout, double* disc, cudaStream_t s, const SketchRef* sk,
+                       TuneEntry* out) {
+  const int sms = num_sms();
+  const int nbs[3] = {32, 16, 8};
+  const int ctas[3] = {sms, std::max(1, sms * 3 / 4), std::max(1, sms / 2)};
+  cudaEvent_t e0, e1;
+  CKE(cudaEventCreate(&e0));
+  cudaError_t err = cudaEventCreate(&e1);
+  if (err != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return err;
+  }
+  auto run = [&](const Knobs& kn, int reps, float* best) -> cudaError_t {
+    *best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      CKE(cudaEventRecord(e0, s));
+      CKE(two_site_core<T>(w, kn, cl, cm, cr, chi, A, B, g, Aout, Bout, disc, nullptr, s, nullptr, sk));
+      CKE(cudaEventRecord(e1, s));
+      CKE(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CKE(cudaEventElapsedTime(&ms, e0, e1));
+      *best = std::min(*best, ms);
+    }
+    return cudaSuccess;
+  };
+  float t_def = 0.f;
+  err = run(base, 1, &t_def);  // warm-up (first-use set-up of the kernels)
+  int reps = 3;
+  if (err == cudaSuccess) {
+    err = run(base, 1, &t_def);
+    reps = t_def > 50.f ? 1 : 3;
+  }
+  float t_best = 1e30f;
+  int best_nb = base.nb, best_g = base.G, cand = 0;
+  for (int a = 0; a < 3 && err == cudaSuccess; ++a)
+    for (int b = 0; b < 3 && err == cudaSuccess; ++b) {
+      if (nbs[a] > base.nb || ctas[b] > base.G) continue;
+      Knobs kn = base;
+      kn.nb = nbs[a];
+      kn.G = ctas[b];
+      float t = 0.f;
+      err = run(kn, reps, &t);
+      ++cand;
+      if (err == cudaSuccess && t < t_best) {
+        t_best = t;
+        best_nb = kn.nb;
+        best_g = kn.G;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return err;
+  out->m = 2 * cl;
+  out->n = 2 * cr;
+  out->k = std::min(std::min(2 * cl, 2 * cr), chi);
+  out->sms = sms;
+  out->nb = best_nb;
+  out->ctas = best_g;
+  out->ms = t_best;
+  out->default_ms = t_def;
+  out->candidates = cand;
+  return cudaSuccess;
+}
+
+// Knobs of the split of gate g on (i, i+1) of a handle: the defaults, or with
+// MPS_FLAG_AUTOTUNE the cached choice for the shape, tuned now (on the handle's
+// stream and workspace, outputs to scratch, the state untouched) if there is none.
+template <typename T>
+int tuned_knobs(mps_t h, int i, const T* gt, int chi, const SketchRef* sk, Knobs* kn) {
+  *kn = h->kn;
+  if (!h->tune || h->trunc == MPS_TRUNC_SVD) return MPS_OK;
+  const int cl = h->bond[i], cm = h->bond[i + 1], cr = h->bond[i + 2];
+  const int m = 2 * cl, n = 2 * cr, k = std::min(std::min(m, n), chi);
+  TuneEntry e;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (TuneEntry* hit = tune_find_locked(h->prec, m, n, k, num_sms())) {
+      e = *hit;
+      have = true;
+    }
+  }
+  if (!have) {
+    if (!h->tune_ws) {
+      h->tune_half = align_up(h->esz * 2 * (size_t)h->chicap * h->chicap);
+      h->tune_ws = (char*)dev_alloc(h, 2 * h->tune_half + kAlign);
+      if (!h->tune_ws) return fail(h, MPS_E_NOMEM, "autotune: scratch");
+    }
+    cudaError_t err = tune_split<T>(views<T>(h), h->kn, cl, cm, cr, chi, (const T*)h->site[i],
+                                    (const T*)h->site[i + 1], gt, (T*)h->tune_ws, (T*)(h->tune_ws + h->tune_half),
+                                    (double*)(h->tune_ws + 2 * h->tune_half), h->stream, sk, &e);
+    if (err != cudaSuccess) return cuda_fail(h, err, "autotune");
+    e.prec = h->prec;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_store_locked(e);
+  }
+  kn->nb = std::min(e.nb, h->kn.nb);
+  kn->G = std::min(e.ctas, h->kn.G);
   return MPS_OK;
 }
 
@@ -719,19 +915,20 @@ int apply_2q_t(mps_t h, int i, const mps_c128* g, int chi) {
   double* slot = h->d_disclog + (h->nsplit % kDiscLog);
   cudaError_t e;
   h->piv_n = 0;
+  SketchRef sk;
+  sk.base = h->sk_ws;
+  sk.L = &h->SKL;
+  sk.seed = h->sketch_seed + (unsigned long long)h->nsplit;  // split number s: seed + s
+  const SketchRef* skp = h->trunc == MPS_TRUNC_RQRCP ? &sk : nullptr;
+  Knobs kn;
+  int rc = tuned_knobs<T>(h, i, gt, chi, skp, &kn);
+  if (rc) return rc;
   if (h->trunc == MPS_TRUNC_SVD)
-    e = two_site_svd<T>(w, h->svd_ws, h->SL, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1],
+    e = two_site_svd<T>(w, h->svd_ws, h->SL, kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1],
                         gt, (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
-  else if (h->trunc == MPS_TRUNC_RQRCP) {
-    SketchRef sk;
-    sk.base = h->sk_ws;
-    sk.L = &h->SKL;
-    sk.seed = h->sketch_seed + (unsigned long long)h->nsplit;  // split number s: seed + s
-    e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
-                         (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks, &sk);
-  } else
-    e = two_site_core<T>(w, h->kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
-                         (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks);
+  else
+    e = two_site_core<T>(w, kn, cl, cm, cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
+                         (T*)h->site[i], (T*)h->site[i + 1], slot, h->d_scalar + 1, h->stream, &h->prof.hooks, skp);
   if (e != cudaSuccess) return cuda_fail(h, e, "apply_2q");
   if (h->trunc != MPS_TRUNC_SVD) {
     h->piv_n = 2 * cr;
@@ -928,6 +1125,14 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
     (2 * it.cl <= kLaneDim && 2 * it.cr <= kLaneDim ? small : big).push_back(it);
   }
   std::sort(small.begin(), small.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
+  // split knobs per gate (autotuned shapes are tuned here, before any lane starts)
+  std::vector<Knobs> kj(count);
+  for (int j = 0; j < count; ++j) {
+    T gt[16];
+    gate_to_T<T>(gates + 16 * j, 16, gt);
+    rc = tuned_knobs<T>(h, sites[j], gt, chi, nullptr, &kj[j]);
+    if (rc) return rc;
+  }
   const int64_t first = h->nsplit;
   auto slot_of = [&](int j) { return h->d_disclog + ((first + j) % kDiscLog); };
   CUTRY(h, cudaEventRecord(h->ev_fork, h->stream), "layer fork");
@@ -951,8 +1156,8 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
     T gt[16];
     gate_to_T<T>(gates + 16 * it.j, 16, gt);
     const int i = sites[it.j];
-    Knobs kl = h->kn;
-    kl.G = std::min(h->kn.G, std::max((2 * it.cl + 127) / 128, share));
+    Knobs kl = kj[it.j];
+    kl.G = std::min(kl.G, std::max((2 * it.cl + 127) / 128, share));
     cudaError_t e = two_site_core<T>(w, kl, it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
                                      (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1],
                                      slot_of(it.j), nullptr, ln.stream, &h->prof.hooks);
@@ -962,7 +1167,7 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
     T gt[16];
     gate_to_T<T>(gates + 16 * it.j, 16, gt);
     const int i = sites[it.j];
-    cudaError_t e = two_site_core<T>(views<T>(h), h->kn, it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
+    cudaError_t e = two_site_core<T>(views<T>(h), kj[it.j], it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
                                      (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1],
                                      slot_of(it.j), nullptr, h->stream, &h->prof.hooks);
     if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer");
@@ -1302,6 +1507,7 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   h->kn.barrier_extra = (unsigned)cfg.debug_barrier_extra;
   h->prof.enabled = (cfg.flags & MPS_FLAG_PROFILE) != 0;
   h->kn.use_tc = h->prec == MPS_PREC_MIXED && (cfg.flags & MPS_FLAG_TENSOR_CORES) != 0;
+  h->tune = (cfg.flags & MPS_FLAG_AUTOTUNE) != 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -1786,6 +1992,109 @@ int mps_kernel_stats_reset(mps_t h) {
   cudaStreamSynchronize(h->stream);
   h->prof.drain();
   memset(h->prof.stat, 0, sizeof(h->prof.stat));
+  return MPS_OK;
+}
+
+// ---- autotuner entry point
+int mps_tune_two_site(int precision, int chi_l, int chi_m, int chi_r, int chi_max, int force, mps_tune_result* out) {
+  if (!out || chi_l < 1 || chi_m < 1 || chi_r < 1 || chi_max < 1) return MPS_E_ARG;
+  if (precision != MPS_PREC_FP64 && precision != MPS_PREC_MIXED) return MPS_E_ARG;
+  const int m = 2 * chi_l, n = 2 * chi_r, k = std::min(std::min(m, n), chi_max);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return MPS_E_CUDA;
+  }
+  const int sms = num_sms();
+  if (!force) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (TuneEntry* hit = tune_find_locked(precision, m, n, k, sms)) {
+      out->panel_width = hit->nb;
+      out->panel_ctas = hit->ctas;
+      out->candidates = 0;
+      out->ms = hit->ms;
+      out->default_ms = hit->default_ms;
+      return MPS_OK;
+    }
+  }
+  const size_t esz = precision == MPS_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+  int64_t ldw, ldq;
+  WsLayout L = ws_layout(esz, m, n, k, kDefaultNb, kMaxCoop, ldw, ldq);
+  const int64_t na = (int64_t)m * chi_m, nbb = (int64_t)chi_m * n, no = (int64_t)std::max(m, n) * k;
+  char *ws = nullptr, *bufs = nullptr;
+  cudaStream_t s = nullptr;
+  int rc = MPS_OK;
+  const size_t off_b = align_up(esz * na), off_oa = off_b + align_up(esz * nbb), off_ob = off_oa + align_up(esz * no),
+               off_d = off_ob + align_up(esz * no), off_tmp = off_d + kAlign;
+  if (cudaMalloc(&ws, L.total) != cudaSuccess ||
+      cudaMalloc(&bufs, off_tmp + align_up(sizeof(c64) * std::max(na, nbb))) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    rc = MPS_E_NOMEM;
+  }
+  TuneEntry e;
+  if (rc == MPS_OK) {
+    cudaMemsetAsync(ws + L.bar, 0, 16, s);
+    cudaMemsetAsync(ws + L.err, 0, 16, s);
+    Knobs kn;
+    kn.nb = kDefaultNb;
+    kn.G = std::min(sms, kMaxCoop);
+    kn.flag_tol = precision == MPS_PREC_FP64 ? 1.4901161193847656e-08 : 1e-3;
+    kn.timeout_ns = kRawTimeoutNs;
+    kn.barrier_extra = 0;
+    kn.use_tc = false;
+    mps_c128 gh[16];
+    for (int q = 0; q < 16; ++q) gh[q] = {q % 5 == 0 ? 1.0 : 0.0, 0.0};  // the identity gate (any gate times the same)
+    c64* tmp = (c64*)(bufs + off_tmp);
+    cudaError_t err = cudaSuccess;
+    // seeded random sites (the work of a split does not depend on the values)
+    for (int which = 0; which < 2 && err == cudaSuccess; ++which) {
+      const int64_t cnt = which ? nbb : na;
+      fill_random_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(tmp, cnt, 101u + which);
+      char* dst = bufs + (which ? off_b : 0);
+      err = precision == MPS_PREC_FP64 ? convert<c128, c64>(tmp, (c128*)dst, cnt, s)
+                                       : cudaMemcpyAsync(dst, tmp, sizeof(c64) * cnt, cudaMemcpyDeviceToDevice, s);
+    }
+    if (err == cudaSuccess) {
+      if (precision == MPS_PREC_FP64) {
+        c128 gt[16];
+        gate_to_T<c128>(gh, 16, gt);
+        err = tune_split<c128>(ws_views<c128>(ws, L, ldw, ldq), kn, chi_l, chi_m, chi_r, chi_max, (const c128*)bufs,
+                               (const c128*)(bufs + off_b), gt, (c128*)(bufs + off_oa), (c128*)(bufs + off_ob),
+                               (double*)(bufs + off_d), s, nullptr, &e);
+      } else {
+        c64 gt[16];
+        gate_to_T<c64>(gh, 16, gt);
+        err = tune_split<c64>(ws_views<c64>(ws, L, ldw, ldq), kn, chi_l, chi_m, chi_r, chi_max, (const c64*)bufs,
+                              (const c64*)(bufs + off_b), gt, (c64*)(bufs + off_oa), (c64*)(bufs + off_ob),
+                              (double*)(bufs + off_d), s, nullptr, &e);
+      }
+    }
+    int dev_err = 0;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&dev_err, ws + L.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      rc = MPS_E_CUDA;
+    } else if (dev_err != DEV_OK) {
+      rc = dev_err == DEV_ERR_TIMEOUT ? MPS_E_TIMEOUT : MPS_E_CUDA;
+    }
+  }
+  if (s) cudaStreamDestroy(s);
+  cudaFree(ws);
+  cudaFree(bufs);
+  if (rc != MPS_OK) return rc;
+  e.prec = precision;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_find_locked(precision, m, n, k, sms);  // loads the file's entries first
+    tune_store_locked(e);
+  }
+  out->panel_width = e.nb;
+  out->panel_ctas = e.ctas;
+  out->candidates = e.candidates;
+  out->ms = e.ms;
+  out->default_ms = e.default_ms;
   return MPS_OK;
 }
 

@@ -30,7 +30,7 @@ def _gate(g, n):
 
 def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile=False,
            wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False, debug_max_ctas=0,
-           truncation="qrcp", sketch_seed=0):
+           truncation="qrcp", sketch_seed=0, autotune=False):
     lib = L.load()
     cfg = L.mps_config()
     lib.mps_config_init(ctypes.byref(cfg))
@@ -38,7 +38,8 @@ def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile
     cfg.policy = {"canon": L.MPS_POLICY_CANON, "local": L.MPS_POLICY_LOCAL}[policy]
     cfg.panel_width = panel_width
     cfg.stream = stream
-    cfg.flags = (L.MPS_FLAG_PROFILE if profile else 0) | (L.MPS_FLAG_TENSOR_CORES if tensor_cores else 0)
+    cfg.flags = ((L.MPS_FLAG_PROFILE if profile else 0) | (L.MPS_FLAG_TENSOR_CORES if tensor_cores else 0)
+                 | (L.MPS_FLAG_AUTOTUNE if autotune else 0))
     cfg.wait_timeout_s = wait_timeout_s
     cfg.device = device
     cfg.debug_barrier_extra = debug_barrier_extra
@@ -242,3 +243,16 @@ class MPS:
 
     def kernel_stats_reset(self):
         self._check(self.lib.mps_kernel_stats_reset(self.h))
+
+
+def tune_two_site(precision, chi_l, chi_m, chi_r, chi_max, force=False):
+    """Autotune one two-site split shape (mps_tune_two_site): returns a dict with the
+    chosen panel width and panel CTA count, the candidates timed and the times."""
+    lib = L.load()
+    out = L.mps_tune_result()
+    code = {"fp64": L.MPS_PREC_FP64, "mixed": L.MPS_PREC_MIXED}[precision]
+    rc = lib.mps_tune_two_site(code, chi_l, chi_m, chi_r, chi_max, 1 if force else 0, ctypes.byref(out))
+    if rc != 0:
+        raise MPSError(rc, "mps_tune_two_site failed")
+    return {"panel_width": out.panel_width, "panel_ctas": out.panel_ctas, "candidates": out.candidates,
+            "ms": out.ms, "default_ms": out.default_ms}
