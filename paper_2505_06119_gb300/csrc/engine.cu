@@ -162,7 +162,27 @@ struct Knobs {
   unsigned long long timeout_ns;
   unsigned barrier_extra;
   bool use_tc;  // complex64 products on the tensor cores
+  bool small;   // splits whose theta fits one CTA run in small_gate_kernel
 };
+
+template <typename T>
+SmallGate<T> small_item(int cl, int cm, int cr, int k, const T* A, const T* B, const T* g, T* Aout, T* Bout,
+                        double* disc, double* disc_total, int* jpvt_out) {
+  SmallGate<T> it;
+  it.A = A;
+  it.B = B;
+  it.Aout = Aout;
+  it.Bout = Bout;
+  it.disc = disc;
+  it.disc_total = disc_total;
+  it.jpvt_out = jpvt_out;
+  it.cl = cl;
+  it.cm = cm;
+  it.cr = cr;
+  it.k = k;
+  for (int q = 0; q < 16; ++q) it.g[q] = g[q];
+  return it;
+}
 
 template <typename T>
 QrPlan<T> make_plan(const Ws<T>& w, const Knobs& kn, int m, int n, int k, int pivot, double* disc_slot,
@@ -248,6 +268,17 @@ cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int c
                           LaunchHooks* hk, const SketchRef* sk = nullptr) {
   const int m = 2 * cl, n = 2 * cr;
   const int k = std::min(std::min(m, n), chi);
+  if (!sk && kn.small && small_gate_fits(cl, cm, cr)) {
+    // the whole split in one CTA
+    SmallBatch<T> b;
+    b.count = 1;
+    b.item[0] = small_item<T>(cl, cm, cr, k, A, B, g, Aout, Bout, disc_slot, disc_total, w.jpvt);
+    hook_before(hk, MPS_KCLASS_PANEL, ((double)m * cm + (double)cm * n + 2.0 * (m + n) * k) * sizeof(T),
+                8.0 * m * n * cm + 16.0 * m * n * k + 8.0 * m * k * k);
+    CKE(small_gate_launch<T>(b, s));
+    hook_after(hk, MPS_KCLASS_PANEL, 1);
+    return cudaSuccess;
+  }
   CKE(theta_step<T>(w, kn, cl, cm, cr, A, B, g, s, hk));
   QrPlan<T> p = make_plan<T>(w, kn, m, n, k, 1, disc_slot, disc_total);
   if (sk) plan_sketch<T>(p, *sk);
@@ -756,6 +787,7 @@ int tuned_knobs(mps_t h, int i, const T* gt, int chi, const SketchRef* sk, Knobs
   *kn = h->kn;
   if (!h->tune || h->trunc == MPS_TRUNC_SVD) return MPS_OK;
   const int cl = h->bond[i], cm = h->bond[i + 1], cr = h->bond[i + 2];
+  if (h->kn.small && h->trunc == MPS_TRUNC_QRCP && small_gate_fits(cl, cm, cr)) return MPS_OK;  // one CTA: no knobs
   const int m = 2 * cl, n = 2 * cr, k = std::min(std::min(m, n), chi);
   TuneEntry e;
   bool have = false;
@@ -1111,7 +1143,7 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
     int j, cl, cm, cr, k;
     double work;
   };
-  std::vector<Item> small, big;
+  std::vector<Item> small, big, tiny;
   for (int j = 0; j < count; ++j) {
     const int i = sites[j];
     Item it;
@@ -1122,7 +1154,10 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
     it.k = std::min(std::min(2 * it.cl, 2 * it.cr), chi);
     const double m = 2.0 * it.cl, n = 2.0 * it.cr;
     it.work = m * n * (it.cm + it.k) + 1e6;  // contraction + factorisation, plus a fixed latency share
-    (2 * it.cl <= kLaneDim && 2 * it.cr <= kLaneDim ? small : big).push_back(it);
+    if (h->kn.small && small_gate_fits(it.cl, it.cm, it.cr))
+      tiny.push_back(it);  // one CTA each, all in one grouped launch
+    else
+      (2 * it.cl <= kLaneDim && 2 * it.cr <= kLaneDim ? small : big).push_back(it);
   }
   std::sort(small.begin(), small.end(), [](const Item& a, const Item& b) { return a.work > b.work; });
   // split knobs per gate (autotuned shapes are tuned here, before any lane starts)
@@ -1163,6 +1198,21 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
                                      slot_of(it.j), nullptr, ln.stream, &h->prof.hooks);
     if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer");
   }
+  // the gates whose theta fits one CTA: one grouped launch per kSmallBatch of them
+  for (size_t b0 = 0; b0 < tiny.size(); b0 += kSmallBatch) {
+    SmallBatch<T> sb;
+    sb.count = (int)std::min<size_t>(kSmallBatch, tiny.size() - b0);
+    for (int q = 0; q < sb.count; ++q) {
+      const Item& it = tiny[b0 + q];
+      T gt[16];
+      gate_to_T<T>(gates + 16 * it.j, 16, gt);
+      const int i = sites[it.j];
+      sb.item[q] = small_item<T>(it.cl, it.cm, it.cr, it.k, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
+                                 (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr, nullptr);
+    }
+    cudaError_t e = small_gate_launch<T>(sb, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer: small gates");
+  }
   for (const Item& it : big) {
     T gt[16];
     gate_to_T<T>(gates + 16 * it.j, 16, gt);
@@ -1181,6 +1231,7 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
   CUTRY(h, cudaGetLastError(), "layer discarded");
   for (const Item& it : small) h->bond[sites[it.j] + 1] = it.k;
   for (const Item& it : big) h->bond[sites[it.j] + 1] = it.k;
+  for (const Item& it : tiny) h->bond[sites[it.j] + 1] = it.k;
   h->nsplit += count;
   return MPS_OK;
 }
@@ -1508,6 +1559,9 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   h->prof.enabled = (cfg.flags & MPS_FLAG_PROFILE) != 0;
   h->kn.use_tc = h->prec == MPS_PREC_MIXED && (cfg.flags & MPS_FLAG_TENSOR_CORES) != 0;
   h->tune = (cfg.flags & MPS_FLAG_AUTOTUNE) != 0;
+  // the debug knobs exercise the grid kernels' barriers and row loops, which the
+  // one-CTA path of small splits does not have
+  h->kn.small = cfg.debug_barrier_extra == 0 && cfg.debug_max_ctas == 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -2043,6 +2097,7 @@ int mps_tune_two_site(int precision, int chi_l, int chi_m, int chi_r, int chi_ma
     kn.timeout_ns = kRawTimeoutNs;
     kn.barrier_extra = 0;
     kn.use_tc = false;
+    kn.small = false;  // time the multi-kernel split itself
     mps_c128 gh[16];
     for (int q = 0; q < 16; ++q) gh[q] = {q % 5 == 0 ? 1.0 : 0.0, 0.0};  // the identity gate (any gate times the same)
     c64* tmp = (c64*)(bufs + off_tmp);
@@ -2141,6 +2196,7 @@ int mps_two_site_apply(int precision, int chi_l, int chi_m, int chi_r, int chi_m
   kn.timeout_ns = g_raw_timeout_ns.load(std::memory_order_relaxed);
   kn.barrier_extra = (unsigned)g_raw_barrier_extra.load(std::memory_order_relaxed);
   kn.use_tc = false;
+  kn.small = kn.barrier_extra == 0;
   double* slot = discarded_dev ? discarded_dev : (double*)(base + L.disc);
   cudaError_t e;
   if (precision == MPS_PREC_FP64) {

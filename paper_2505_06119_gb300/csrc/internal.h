@@ -197,6 +197,36 @@ struct QrPlan {
 // sketch rows beyond the block size (oversampling) of the randomized QRCP
 constexpr int kSketchOversample = 8;
 
+// ---------------------------------------------------------------------------
+// Small two-site gates (small_gate.cu): theta of at most kSmallDim x kSmallDim
+// split entirely in one CTA; a batch is one grouped launch, one CTA per gate.
+constexpr int kSmallDim = 64;
+constexpr int kSmallMaxCm = 256;
+constexpr int kSmallBatch = 32;
+
+template <typename T>
+struct SmallGate {
+  const T* A;          // site i, row-major (cl, 2, cm)
+  const T* B;          // site i+1, row-major (cm, 2, cr)
+  T* Aout;             // (cl, 2, k); may alias A
+  T* Bout;             // (k, 2, cr); may alias B
+  double* disc;        // discarded weight of this split
+  double* disc_total;  // optional: the discarded weight is also added here
+  int* jpvt_out;       // optional: the pivot order (2 cr entries)
+  int cl, cm, cr, k;
+  T g[16];             // gate, g[(2a+b)*4 + (2c+d)]
+};
+
+template <typename T>
+struct SmallBatch {
+  int count;
+  SmallGate<T> item[kSmallBatch];
+};
+
+bool small_gate_fits(int cl, int cm, int cr);
+template <typename T>
+cudaError_t small_gate_launch(const SmallBatch<T>& b, cudaStream_t s);
+
 struct LaunchHooks;  // profiling hooks (engine.cu)
 
 template <typename T>

@@ -131,17 +131,25 @@ def test_bounded_wait_expiry_is_reported_and_context_survives():
 
 
 def test_launch_accounting_and_profile():
+    """Launch counts per kernel class: a split above the one-CTA size runs the theta
+    kernel once and one pivoted panel per 32 pivots; a small split is one launch."""
     from paper_2505_06119_gb300 import MPS
 
-    with MPS(8, 16, precision="mixed", profile=True) as m:
-        m.apply_2q(3, gates.haar_unitary(np.random.default_rng(1), 4))
+    rng = np.random.default_rng(1)
+    with MPS(14, 64, precision="mixed", profile=True, policy="local") as m:
+        m.set_site(6, states.complex_gaussian(rng, (64, 2, 64)).astype(np.complex64))
+        m.set_site(7, states.complex_gaussian(rng, (64, 2, 64)).astype(np.complex64))
+        m.apply_2q(6, gates.haar_unitary(rng, 4))
         m.sync()
         st = m.kernel_stats()
         assert st["theta"]["launches"] == 1
-        assert st["panel"]["launches"] >= 1
+        assert st["panel"]["launches"] == 2  # k = 64 pivots, panel width 32
         assert st["panel"]["ms"] > 0
         m.kernel_stats_reset()
         assert m.kernel_stats()["panel"]["launches"] == 0
+        m.apply_2q(0, gates.haar_unitary(rng, 4))  # theta 2 x 4: one CTA
+        st = m.kernel_stats()
+        assert st["panel"]["launches"] == 1 and st["theta"]["launches"] == 0
 
 
 @pytest.mark.parametrize("noalloc", [False, True])

@@ -74,6 +74,12 @@ SPLIT_CASES = [
     (100, 37, 65, 50),
     (130, 70, 129, 128),
     (257, 64, 200, 160),
+    # theta at most 64 x 64: the whole split in one CTA (small_gate_kernel)
+    (32, 32, 32, 32),
+    (32, 32, 32, 20),
+    (20, 64, 32, 16),
+    (32, 200, 31, 64),
+    (5, 1, 30, 64),
 ]
 
 

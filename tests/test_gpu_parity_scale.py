@@ -269,3 +269,39 @@ def test_permute_layers_needs_local_policy():
         with pytest.raises(MPSError) as ei:
             m.permute_layers([1, 0, 2, 3, 4, 5])
         assert ei.value.code == L.MPS_E_STATE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grouped_small_gate_layers_match_oracle(prec):
+    """A 70-qubit chain at chi = 8: every gate of a layer fits one CTA, 34 gates per
+    layer, so a layer is two grouped launches (32 + 2 CTAs).  Against the oracle's
+    local policy: bond dims, and FP64 norm fidelity 1e-9 / amplitudes 1e-10 (mixed:
+    state fidelity >= 1 - 1e-4); and equal to the gates applied one by one, bit for bit."""
+    n, chi = 70, 8
+    layers = circuits.brickwall_layers(n, 6, seed=29)
+    ref = omps.OracleMPS(n, chi, "local")
+    with gpu_mps(n, chi, precision=prec, policy="local") as m, gpu_mps(n, chi, precision=prec,
+                                                                     policy="local") as one:
+        for ones, twos in layers:
+            for q, u in ones:
+                m.apply_1q(q, u)
+                one.apply_1q(q, u)
+                ref.apply_1q(q, u)
+            m.apply_layer([q for q, _ in twos], [g for _, g in twos])
+            for q, g in twos:
+                one.apply_2q(q, g)
+                ref.apply_2q(q, g)
+        assert m.bond_dims() == ref.bond_dims()
+        for i in range(n):
+            assert np.array_equal(m.get_site(i), one.get_site(i))
+        if prec == "fp64":
+            assert m.fidelity() == pytest.approx(ref.norm2(), rel=1e-9)
+            rng = np.random.default_rng(9)
+            for _ in range(8):
+                bits = rng.integers(0, 2, n)
+                assert abs(m.amplitude(bits) - ref.amplitude(bits)) < 1e-10
+        else:
+            got = omps.OracleMPS(n, chi, "local")
+            got.set_sites([m.get_site(i) for i in range(n)])
+            assert abs(got.overlap(ref)) ** 2 / (got.norm2() * ref.norm2()) >= 1 - 1e-4
+    assert ref.norm2() < 0.999

@@ -107,23 +107,24 @@ def test_autotuned_handle_uses_the_choice_and_stays_correct():
     equals the oracle's."""
     from paper_2505_06119_gb300.mps import tune_two_site
 
-    ops = circuits.brickwall(12, 6, seed=23)
-    ref = omps.OracleMPS(12, 32, "local")
+    ops = circuits.brickwall(14, 8, seed=23)
+    ref = omps.OracleMPS(14, 64, "local")
     ref.run(ops)
-    with gpu_mps(12, 32, precision="fp64", policy="local", autotune=True) as m:
+    with gpu_mps(14, 64, precision="fp64", policy="local", autotune=True) as m:
         m.run(ops)
         assert m.fidelity() == pytest.approx(ref.norm2(), rel=1e-9)
         rng = np.random.default_rng(2)
         for _ in range(16):
-            bits = rng.integers(0, 2, 12)
+            bits = rng.integers(0, 2, 14)
             assert abs(m.amplitude(bits) - ref.amplitude(bits)) < 1e-10
-    # the choice for a 64 x 64 split with k = 32 is now cached; a profiled handle uses it
-    choice = tune_two_site("fp64", 32, 32, 32, 32)
-    with gpu_mps(12, 32, precision="fp64", policy="local", autotune=True, profile=True) as m:
+    assert max(ref.bond_dims()) == 64  # splits above the one-CTA size were tuned
+    # the choice for a 96 x 96 split with k = 48 is cached now; a profiled handle uses it
+    choice = tune_two_site("fp64", 48, 48, 48, 48)
+    with gpu_mps(14, 64, precision="fp64", policy="local", autotune=True, profile=True) as m:
         rng = np.random.default_rng(4)
-        m.set_site(5, states.complex_gaussian(rng, (32, 2, 32)))
-        m.set_site(6, states.complex_gaussian(rng, (32, 2, 32)))
+        m.set_site(5, states.complex_gaussian(rng, (48, 2, 48)))
+        m.set_site(6, states.complex_gaussian(rng, (48, 2, 48)))
         m.kernel_stats_reset()
-        m.apply_2q(5, gates.haar_unitary(rng, 4), 32)
+        m.apply_2q(5, gates.haar_unitary(rng, 4), 48)
         st = m.kernel_stats()
-    assert st["panel"]["launches"] == -(-32 // choice["panel_width"])
+    assert st["panel"]["launches"] == -(-48 // choice["panel_width"])
