@@ -583,8 +583,9 @@ def lapack_workload(args):
 def layer_workload(args):
     """Layer batching (a 64-qubit chain, bonds 2..chi, random canonical state, mixed
     precision, LOCAL policy): one brick-wall layer of Haar SU(4) gates on the even and
-    on the odd bonds, applied by mps_apply_layer and one gate at a time; per-layer
-    milliseconds of each (CUDA-synchronised wall clock, after one warm-up layer)."""
+    on the odd bonds, applied by mps_apply_layer (replayed as a CUDA graph, and with
+    direct launches) and one gate at a time; per-layer milliseconds of each
+    (CUDA-synchronised wall clock, after two warm-up layers)."""
     import numpy as np
     import torch
 
@@ -605,22 +606,26 @@ def layer_workload(args):
             bonds = list(range(par, n - 1, 2))
             gs = [gates.haar_unitary(rng, 4) for _ in bonds]
             res = {}
-            for mode in ("layer", "one_by_one"):
-                with MPS(n, chi, precision="mixed", policy="local") as m:
-                    for rep in range(2):  # warm-up layer, then the timed one
+            for mode in ("layer", "layer_direct", "one_by_one"):
+                with MPS(n, chi, precision="mixed", policy="local", graphs=(mode == "layer")) as m:
+                    for rep in range(3):  # two warm-up layers (the second one captures the graph), then timed
                         m.set_sites(sites, centre=n // 2)
                         m.sync()
                         torch.cuda.synchronize()
                         t = time.perf_counter()
-                        if mode == "layer":
+                        if mode != "one_by_one":
                             m.apply_layer(bonds, gs)
                         else:
                             for q, g in zip(bonds, gs):
                                 m.apply_2q(q, g)
                         m.sync()
                         res[mode] = (time.perf_counter() - t) * 1e3
+                    if mode == "layer":
+                        res["graph_launches"] = m.layer_stats()[1]
             row["even" if par == 0 else "odd"] = {"gates": len(bonds), "ms_layer": res["layer"],
+                                                  "ms_layer_direct": res["layer_direct"],
                                                   "ms_one_by_one": res["one_by_one"],
+                                                  "graph_launches": res["graph_launches"],
                                                   "speedup": res["one_by_one"] / res["layer"]}
         out["rows"].append(row)
     print(json.dumps(out), flush=True)

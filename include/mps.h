@@ -104,6 +104,8 @@ extern "C" {
                                        the candidates on the first split of that shape (see
                                        mps_tune_two_site); layers use the choice too.  Off by default: the
                                        choice can change the rounding, though not the bars of the results. */
+#define MPS_FLAG_NO_GRAPH 8         /* issue every mps_apply_layer call directly instead of capturing
+                                       it into a CUDA graph (see mps_apply_layer) */
 #define MPS_FLAG_TENSOR_CORES 2     /* mixed precision: long-K complex products (theta, centre-move
                                        absorption) on the tcgen05 tensor cores with 3xTF32 splitting.
                                        Off by default: the tensor cores' FP32 accumulation drifts
@@ -205,10 +207,16 @@ int mps_permute_layers(mps_t h, const int* order, int chi_max, long long* swaps,
  * sites[j], sites[j]+1 (gates[16*j .. 16*j+15]) (the gates of a brick-wall
  * layer, Sec. III-D; network parallelism, Sec. I).  Requires MPS_POLICY_LOCAL
  * (no centre moves, so the gates commute exactly).  Gates whose two-site block
- * is at most 4096 x 4096 run concurrently on eight internal streams, each with
- * its own workspace (allocated through the handle's allocator at the first
- * call, about 8 x the workspace of a chi = 2048 split); larger ones run in
- * order on the handle's stream, which waits for all of them before returning.
+ * fits one CTA (at most 64 x 64) run together as one grouped launch, one CTA
+ * per gate (32 gates per launch); gates whose block is at most 4096 x 4096 run
+ * concurrently on eight internal streams, each with its own workspace
+ * (allocated through the handle's allocator at the first call, about 8 x the
+ * workspace of a chi = 2048 split); larger ones run in order on the handle's
+ * stream, which waits for all of them before returning.  From the second call
+ * on, the layer's launches are captured into a CUDA graph and replayed; a
+ * layer of the same shape (sites, bond dims, bond cap) reuses the handle's
+ * executable graph, updated with the new gates (MPS_FLAG_NO_GRAPH: direct
+ * launches; a stream that cannot be captured turns graphs off for the handle).
  * The result equals applying the gates one by one, bit for bit; with
  * MPS_FLAG_PROFILE the gates run one by one.  Asynchronous; errors as for
  * mps_apply_2q.  chi_max as for mps_apply_2q. */
@@ -296,6 +304,10 @@ int mps_set_stream(mps_t h, void* stream);
 int mps_sync(mps_t h);
 /* Last error message of the handle ("" if none).  Valid until the next call. */
 const char* mps_last_error(mps_t h);
+
+/* Layer calls so far, how many of them ran as a CUDA graph launch, and whether
+ * graphs are still on for the handle (any pointer may be NULL). */
+int mps_layer_stats(mps_t h, long long* layers, long long* graph_launches, int* graphs_on);
 
 /* Kernel classes tracked by mps_kernel_stats. */
 #define MPS_KCLASS_THETA 0  /* theta contraction + gate epilogue */

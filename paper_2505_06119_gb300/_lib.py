@@ -30,6 +30,7 @@ MPS_HOST_C64 = 1
 MPS_FLAG_PROFILE = 1
 MPS_FLAG_TENSOR_CORES = 2
 MPS_FLAG_AUTOTUNE = 4
+MPS_FLAG_NO_GRAPH = 8
 MPS_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 KCLASS = ["theta", "panel", "update", "norms", "formq", "split", "other", "canon", "svd"]
@@ -103,6 +104,8 @@ SIGNATURES = {
     "mps_last_error": (ctypes.c_char_p, [_P]),
     "mps_kernel_stats": (_I, [_P, ctypes.POINTER(mps_kstat)]),
     "mps_kernel_stats_reset": (_I, [_P]),
+    "mps_layer_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(_I)]),
     "mps_two_site_workspace": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "mps_two_site_apply": (_I, [_I, _I, _I, _I, _I, _P, _P, ctypes.POINTER(mps_c128), _P, _P,
                                 _P, _P, ctypes.c_size_t, _P]),

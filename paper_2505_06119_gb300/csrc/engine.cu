@@ -484,6 +484,12 @@ struct Lane {
   int64_t ldw = 0, ldq = 0;
 };
 
+struct GraphSlot {
+  std::string key;  // layer shape: precision, bond cap, (site, bond dims) per gate
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
+
 struct mps_s {
   int n = 0, chi_max = 0, prec = MPS_PREC_FP64, policy = MPS_POLICY_CANON, device = 0;
   cudaStream_t stream = nullptr, own_stream = nullptr;
@@ -528,6 +534,10 @@ struct mps_s {
   // layer path (lazy)
   std::vector<Lane> lanes;
   cudaEvent_t ev_fork = nullptr;
+  bool graphs = true;           // layers are captured into CUDA graphs after the first call
+  long long layer_calls = 0;
+  long long graph_launches = 0;  // layers run as a graph launch
+  std::vector<GraphSlot> graph_cache;
   // autotuning (MPS_FLAG_AUTOTUNE): scratch outputs of the timed candidate splits
   bool tune = false;
   char* tune_ws = nullptr;
@@ -583,6 +593,9 @@ void release(mps_t h) {
     if (ln.done) cudaEventDestroy(ln.done);
   }
   h->lanes.clear();
+  for (GraphSlot& g : h->graph_cache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graph_cache.clear();
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   h->ev_fork = nullptr;
   h->prof.destroy();
@@ -1126,6 +1139,39 @@ int lanes_ready(mps_t h) {
   return MPS_OK;
 }
 
+// Launch a captured layer graph through the handle's cache of executable graphs
+// (one per layer shape, at most kGraphCache): update the cached one in place when
+// the topology matches, else instantiate anew.
+constexpr size_t kGraphCache = 16;
+
+cudaError_t graph_launch(mps_t h, const std::string& key, cudaGraph_t graph) {
+  GraphSlot* slot = nullptr;
+  for (GraphSlot& g : h->graph_cache)
+    if (g.key == key) slot = &g;
+  if (slot) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(slot->exec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(slot->exec);
+      slot->exec = nullptr;
+      CKE(cudaGraphInstantiate(&slot->exec, graph, 0));
+    }
+  } else {
+    if (h->graph_cache.size() >= kGraphCache) {
+      cudaGraphExecDestroy(h->graph_cache.front().exec);
+      h->graph_cache.erase(h->graph_cache.begin());
+    }
+    GraphSlot g;
+    g.key = key;
+    CKE(cudaGraphInstantiate(&g.exec, graph, 0));
+    h->graph_cache.push_back(g);
+    slot = &h->graph_cache.back();
+  }
+  slot->launches++;
+  h->graph_launches++;
+  return cudaGraphLaunch(slot->exec, h->stream);
+}
+
 template <typename T>
 int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi) {
   // per-class event timing needs one stream; the SVD split has one scratch per handle
@@ -1170,65 +1216,100 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
   }
   const int64_t first = h->nsplit;
   auto slot_of = [&](int j) { return h->d_disclog + ((first + j) % kDiscLog); };
-  CUTRY(h, cudaEventRecord(h->ev_fork, h->stream), "layer fork");
-  std::vector<double> load(kLanes, 0.0);
-  std::vector<char> used(kLanes, 0);
   const int* err_main = views<T>(h).err;
   // lane gates share the SMs: each panel kernel gets a slice of them, but at
   // least one CTA per 128 rows of theta, with which the per-CTA partial sums of
   // every panel step are those of a full grid, so results do not change.
   const int share = num_sms() / std::max(1, std::min<int>((int)small.size(), kLanes));
-  for (const Item& it : small) {
-    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    Lane& ln = h->lanes[l];
-    if (!used[l]) {
-      CUTRY(h, cudaStreamWaitEvent(ln.stream, h->ev_fork, 0), "layer fork");
-      used[l] = 1;
-    }
-    load[l] += it.work;
-    Ws<T> w = ws_views<T>(ln.ws, ln.L, ln.ldw, ln.ldq);
-    w.err = const_cast<int*>(err_main);  // one error word per handle
-    T gt[16];
-    gate_to_T<T>(gates + 16 * it.j, 16, gt);
-    const int i = sites[it.j];
-    Knobs kl = kj[it.j];
-    kl.G = std::min(kl.G, std::max((2 * it.cl + 127) / 128, share));
-    cudaError_t e = two_site_core<T>(w, kl, it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
-                                     (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1],
-                                     slot_of(it.j), nullptr, ln.stream, &h->prof.hooks);
-    if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer");
-  }
-  // the gates whose theta fits one CTA: one grouped launch per kSmallBatch of them
-  for (size_t b0 = 0; b0 < tiny.size(); b0 += kSmallBatch) {
-    SmallBatch<T> sb;
-    sb.count = (int)std::min<size_t>(kSmallBatch, tiny.size() - b0);
-    for (int q = 0; q < sb.count; ++q) {
-      const Item& it = tiny[b0 + q];
+  // Every launch of the layer, in order: the lanes' gates, the grouped launches of
+  // the small gates, the large gates on the handle's stream, the join and the sum
+  // of the discarded weights.  Returns the first failing call's error.
+  auto issue = [&]() -> cudaError_t {
+    CKE(cudaEventRecord(h->ev_fork, h->stream));
+    std::vector<double> load(kLanes, 0.0);
+    std::vector<char> used(kLanes, 0);
+    for (const Item& it : small) {
+      const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      Lane& ln = h->lanes[l];
+      if (!used[l]) {
+        CKE(cudaStreamWaitEvent(ln.stream, h->ev_fork, 0));
+        used[l] = 1;
+      }
+      load[l] += it.work;
+      Ws<T> w = ws_views<T>(ln.ws, ln.L, ln.ldw, ln.ldq);
+      w.err = const_cast<int*>(err_main);  // one error word per handle
       T gt[16];
       gate_to_T<T>(gates + 16 * it.j, 16, gt);
       const int i = sites[it.j];
-      sb.item[q] = small_item<T>(it.cl, it.cm, it.cr, it.k, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
-                                 (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr, nullptr);
+      Knobs kl = kj[it.j];
+      kl.G = std::min(kl.G, std::max((2 * it.cl + 127) / 128, share));
+      CKE(two_site_core<T>(w, kl, it.cl, it.cm, it.cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
+                           (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr, ln.stream, &h->prof.hooks));
     }
-    cudaError_t e = small_gate_launch<T>(sb, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer: small gates");
+    // the gates whose theta fits one CTA: one grouped launch per kSmallBatch of them
+    for (size_t b0 = 0; b0 < tiny.size(); b0 += kSmallBatch) {
+      SmallBatch<T> sb;
+      sb.count = (int)std::min<size_t>(kSmallBatch, tiny.size() - b0);
+      for (int q = 0; q < sb.count; ++q) {
+        const Item& it = tiny[b0 + q];
+        T gt[16];
+        gate_to_T<T>(gates + 16 * it.j, 16, gt);
+        const int i = sites[it.j];
+        sb.item[q] = small_item<T>(it.cl, it.cm, it.cr, it.k, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
+                                   (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr, nullptr);
+      }
+      CKE(small_gate_launch<T>(sb, h->stream));
+    }
+    for (const Item& it : big) {
+      T gt[16];
+      gate_to_T<T>(gates + 16 * it.j, 16, gt);
+      const int i = sites[it.j];
+      CKE(two_site_core<T>(views<T>(h), kj[it.j], it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
+                           (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr,
+                           h->stream, &h->prof.hooks));
+    }
+    for (int l = 0; l < kLanes; ++l) {
+      if (!used[l]) continue;
+      CKE(cudaEventRecord(h->lanes[l].done, h->lanes[l].stream));
+      CKE(cudaStreamWaitEvent(h->stream, h->lanes[l].done, 0));
+    }
+    add_slots_kernel<<<1, 32, 0, h->stream>>>(h->d_disclog, (int)(first % kDiscLog), count, h->d_scalar + 1);
+    return cudaGetLastError();
+  };
+  // After the first layer call (which sets every kernel up), a layer is captured
+  // into a CUDA graph and replayed: the graph of a layer of the same shape (sites,
+  // bond dims, bond cap) is updated in place with this layer's parameters (gates,
+  // discarded-weight slots) and launched as one unit.  If the stream cannot be
+  // captured, the layer is issued directly and graphs stay off for the handle.
+  bool done = false;
+  if (h->graphs && h->layer_calls > 0) {
+    std::string key = std::to_string(h->prec) + ":" + std::to_string(chi);
+    for (int j = 0; j < count; ++j) {
+      const int i = sites[j];
+      key += ";" + std::to_string(i) + "," + std::to_string(h->bond[i]) + "," + std::to_string(h->bond[i + 1]) + "," +
+             std::to_string(h->bond[i + 2]);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t ei = issue();
+      e = cudaStreamEndCapture(h->stream, &graph);
+      if (ei != cudaSuccess) e = ei;
+    }
+    if (e == cudaSuccess && graph) e = graph_launch(h, key, graph);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess) {
+      done = true;
+    } else {
+      cudaGetLastError();
+      h->graphs = false;  // issue directly from now on
+    }
   }
-  for (const Item& it : big) {
-    T gt[16];
-    gate_to_T<T>(gates + 16 * it.j, 16, gt);
-    const int i = sites[it.j];
-    cudaError_t e = two_site_core<T>(views<T>(h), kj[it.j], it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
-                                     (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1],
-                                     slot_of(it.j), nullptr, h->stream, &h->prof.hooks);
+  if (!done) {
+    cudaError_t e = issue();
     if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer");
   }
-  for (int l = 0; l < kLanes; ++l) {
-    if (!used[l]) continue;
-    CUTRY(h, cudaEventRecord(h->lanes[l].done, h->lanes[l].stream), "layer join");
-    CUTRY(h, cudaStreamWaitEvent(h->stream, h->lanes[l].done, 0), "layer join");
-  }
-  add_slots_kernel<<<1, 32, 0, h->stream>>>(h->d_disclog, (int)(first % kDiscLog), count, h->d_scalar + 1);
-  CUTRY(h, cudaGetLastError(), "layer discarded");
+  h->layer_calls++;
   for (const Item& it : small) h->bond[sites[it.j] + 1] = it.k;
   for (const Item& it : big) h->bond[sites[it.j] + 1] = it.k;
   for (const Item& it : tiny) h->bond[sites[it.j] + 1] = it.k;
@@ -1559,6 +1640,7 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
   h->prof.enabled = (cfg.flags & MPS_FLAG_PROFILE) != 0;
   h->kn.use_tc = h->prec == MPS_PREC_MIXED && (cfg.flags & MPS_FLAG_TENSOR_CORES) != 0;
   h->tune = (cfg.flags & MPS_FLAG_AUTOTUNE) != 0;
+  h->graphs = (cfg.flags & MPS_FLAG_NO_GRAPH) == 0;
   // the debug knobs exercise the grid kernels' barriers and row loops, which the
   // one-CTA path of small splits does not have
   h->kn.small = cfg.debug_barrier_extra == 0 && cfg.debug_max_ctas == 0;
@@ -2027,6 +2109,14 @@ int mps_last_split_pivots(mps_t h, int* jpvt, int cap, int* n_out, int* k_out) {
   if (rc) return rc;
   *n_out = h->piv_n;
   *k_out = h->piv_k;
+  return MPS_OK;
+}
+
+int mps_layer_stats(mps_t h, long long* layers, long long* graph_launches, int* graphs_on) {
+  if (!h) return MPS_E_ARG;
+  if (layers) *layers = h->layer_calls;
+  if (graph_launches) *graph_launches = h->graph_launches;
+  if (graphs_on) *graphs_on = h->graphs ? 1 : 0;
   return MPS_OK;
 }
 

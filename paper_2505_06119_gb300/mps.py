@@ -30,7 +30,7 @@ def _gate(g, n):
 
 def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile=False,
            wait_timeout_s=0.0, device=0, debug_barrier_extra=0, tensor_cores=False, debug_max_ctas=0,
-           truncation="qrcp", sketch_seed=0, autotune=False):
+           truncation="qrcp", sketch_seed=0, autotune=False, graphs=True):
     lib = L.load()
     cfg = L.mps_config()
     lib.mps_config_init(ctypes.byref(cfg))
@@ -39,7 +39,7 @@ def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile
     cfg.panel_width = panel_width
     cfg.stream = stream
     cfg.flags = ((L.MPS_FLAG_PROFILE if profile else 0) | (L.MPS_FLAG_TENSOR_CORES if tensor_cores else 0)
-                 | (L.MPS_FLAG_AUTOTUNE if autotune else 0))
+                 | (L.MPS_FLAG_AUTOTUNE if autotune else 0) | (0 if graphs else L.MPS_FLAG_NO_GRAPH))
     cfg.wait_timeout_s = wait_timeout_s
     cfg.device = device
     cfg.debug_barrier_extra = debug_barrier_extra
@@ -240,6 +240,12 @@ class MPS:
         self._check(self.lib.mps_kernel_stats(self.h, arr))
         return {name: {"launches": arr[i].launches, "ms": arr[i].ms, "alg_bytes": arr[i].alg_bytes,
                        "alg_flops": arr[i].alg_flops} for i, name in enumerate(L.KCLASS)}
+
+    def layer_stats(self):
+        """(layer calls, of them run as a CUDA graph launch, graphs still on)."""
+        a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+        self._check(self.lib.mps_layer_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, bool(c.value)
 
     def kernel_stats_reset(self):
         self._check(self.lib.mps_kernel_stats_reset(self.h))

@@ -305,3 +305,28 @@ def test_grouped_small_gate_layers_match_oracle(prec):
             got.set_sites([m.get_site(i) for i in range(n)])
             assert abs(got.overlap(ref)) ** 2 / (got.norm2() * ref.norm2()) >= 1 - 1e-4
     assert ref.norm2() < 0.999
+
+
+@pytest.mark.parametrize("n,chi,prec", [(24, 64, "fp64"), (24, 64, "mixed"), (40, 8, "fp64")])
+def test_layers_replayed_as_cuda_graphs_equal_direct_launches(n, chi, prec):
+    """From the second layer call on, a layer is captured into a CUDA graph and replayed
+    (updated with the new gates); the state equals that of a handle that launches every
+    layer directly, bit for bit, and the brick-wall's repeated layer shapes reuse the
+    graphs."""
+    layers = circuits.brickwall_layers(n, 10, seed=37)
+    with gpu_mps(n, chi, precision=prec, policy="local") as g, gpu_mps(n, chi, precision=prec, policy="local",
+                                                                     graphs=False) as d:
+        for ones, twos in layers:
+            for q, u in ones:
+                g.apply_1q(q, u)
+                d.apply_1q(q, u)
+            sites, gs = [q for q, _ in twos], [u for _, u in twos]
+            g.apply_layer(sites, gs)
+            d.apply_layer(sites, gs)
+        for i in range(n):
+            assert np.array_equal(g.get_site(i), d.get_site(i))
+        assert g.discarded() == d.discarded()
+        calls, graphed, on = g.layer_stats()
+        assert calls == len(layers) and on
+        assert graphed == calls - 1
+        assert d.layer_stats()[1] == 0
