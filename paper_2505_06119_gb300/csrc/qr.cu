@@ -1767,6 +1767,253 @@ __global__ void sketch_solve_kernel(const T* Ys, int64_t ldy, int lsk, int j0, i
   }
 }
 
+// Pivots of one block from the sketch: kb steps of column-pivoted Householder QR
+// on the l x nc matrix Yw (column-major, ld ldy), writing at step j the position
+// p that was swapped with j (the contract of PanelArgs::piv_seq) -- the same
+// pivots as the panel kernel (exact FP64 norms every step instead of downdated
+// ones; exact ties of squared norms go to the lowest original column).
+// Cooperative grid, one grid barrier per step: every CTA keeps its share of the
+// columns in shared memory, publishes its best candidate (norm, column, and the
+// column's entries) in a double-buffered global slot, and after the barrier all
+// CTAs pick the same winner and build the same reflector in FP64, apply it to
+// their columns and recompute their norms.  CTA 0 keeps the position map.
+constexpr int SKT = 256;  // threads of the sketch-pivot kernel
+constexpr int SKW = SKT / 32;
+
+template <typename T>
+struct SketchPivArgs {
+  const T* Y;
+  int64_t ldy;
+  int l, nc, kb;
+  int* piv_seq;
+  int* col_at;   // nc: CTA 0's position map
+  int* pos_of;   // nc
+  T* pub;        // 2 * G * (l + 2) published candidates
+  unsigned* bar;
+  int* err;
+  unsigned expected;
+  unsigned long long timeout_ns;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) {
+  using R = typename real_of<T>::type;
+  extern __shared__ __align__(16) unsigned char sk_smem[];
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int l = a.l;
+  int c0, c1;
+  split_range(0, a.nc, G, b, c0, c1);
+  const int nl = c1 - c0;
+  T* ys = reinterpret_cast<T*>(sk_smem);                          // l x nl, ld l
+  double* nrm = reinterpret_cast<double*>(ys + (int64_t)l * nl);  // nl squared norms (< 0: consumed)
+  T* xw = reinterpret_cast<T*>(nrm + ((nl + 1) & ~1));             // the winner's column, l entries (16-byte aligned)
+  __shared__ double s_bv[SKW];
+  __shared__ int s_bi[SKW];
+  __shared__ int s_win;
+  __shared__ c128 s_tau, s_sc;
+  __shared__ int s_skip;
+  if (tid == 0) s_skip = ld_relaxed_i32(a.err) != DEV_OK;
+  for (int e = tid; e < l * nl; e += SKT) {
+    const int r = e % l, c = e / l;
+    ys[e] = a.Y[r + (int64_t)(c0 + c) * a.ldy];
+  }
+  if (b == 0)
+    for (int c = tid; c < a.nc; c += SKT) {
+      a.col_at[c] = c;
+      a.pos_of[c] = c;
+    }
+  __syncthreads();
+  if (s_skip) return;
+  const int slot = l + 2;  // published entries per CTA: norm, column index, the column
+  for (int j = 0; j < a.kb; ++j) {
+    // exact squared norms of rows j..l-1 of the local columns, one warp per column
+    for (int c = warp; c < nl; c += SKW) {
+      if (j > 0 && nrm[c] < 0.0) continue;  // consumed (lane-uniform)
+      double s2 = 0.0;
+      for (int r = j + lane; r < l; r += 32) {
+        const T x = ys[r + c * l];
+        s2 += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
+      }
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[c] = s2;
+    }
+    __syncthreads();
+    // local candidate: the largest norm, the lowest column on ties
+    double bv = -1.0;
+    int bi = 0x7fffffff;
+    for (int c = tid; c < nl; c += SKT)
+      if (nrm[c] > bv) {  // ascending c per thread
+        bv = nrm[c];
+        bi = c0 + c;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_bv[warp] = bv;
+      s_bi[warp] = bi;
+    }
+    __syncthreads();
+    T* pub = a.pub + ((int64_t)(j & 1) * G + b) * slot;
+    if (tid == 0) {
+      for (int w = 1; w < SKW; ++w)
+        if (s_bv[w] > s_bv[0] || (s_bv[w] == s_bv[0] && s_bi[w] < s_bi[0])) {
+          s_bv[0] = s_bv[w];
+          s_bi[0] = s_bi[w];
+        }
+      pub[0] = mk<R>((R)0, (R)0);
+      reinterpret_cast<double*>(pub)[0] = s_bv[0];  // the norm travels as FP64 bits
+      reinterpret_cast<int*>(pub + 1)[0] = s_bi[0];
+    }
+    __syncthreads();
+    if (s_bi[0] >= c0 && s_bi[0] < c1) {
+      const int c = s_bi[0] - c0;
+      for (int r = tid; r < l; r += SKT) pub[2 + r] = ys[r + c * l];
+    }
+    if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
+    // the winner over all CTAs (identical in every CTA)
+    const T* pset = a.pub + (int64_t)(j & 1) * G * slot;
+    if (warp == 0) {
+      double wv = -1.0;
+      int wi = 0x7fffffff, wb = 0;
+      for (int g = lane; g < G; g += 32) {
+        const double v = reinterpret_cast<const volatile double*>(pset + (int64_t)g * slot)[0];
+        const int i = reinterpret_cast<const volatile int*>(pset + (int64_t)g * slot + 1)[0];
+        if (v > wv || (v == wv && i < wi)) {
+          wv = v;
+          wi = i;
+          wb = g;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, wv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, wb, o);
+        if (ov > wv || (ov == wv && oi < wi)) {
+          wv = ov;
+          wi = oi;
+          wb = ob;
+        }
+      }
+      if (lane == 0) {
+        s_win = wi;
+        s_bi[1] = wb;
+      }
+    }
+    __syncthreads();
+    const int win = s_win, wb = s_bi[1];
+    if (win < 0 || win >= a.nc) {  // only reachable with non-finite norms
+      if (tid == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_NONFINITE);
+      return;
+    }
+    for (int r = tid; r < l; r += SKT) xw[r] = pset[(int64_t)wb * slot + 2 + r];
+    __syncthreads();
+    // reflector of x = winner[j:l] in FP64 (warp 0; the same arithmetic in every CTA)
+    if (warp == 0) {
+      double tail = 0.0;
+      for (int r = j + 1 + lane; r < l; r += 32) {
+        const T x = xw[r];
+        tail += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
+      }
+      tail = warp_sum(tail);
+      if (lane == 0) {
+        const c128 al = ccast<double>(xw[j]);
+        c128 tau, sc;
+        if ((tail == 0.0 && al.im == 0.0) || al.re * al.re + al.im * al.im + tail < zero_column_level<T>()) {
+          tau = mk<double>(0, 0);
+          sc = mk<double>(0, 0);
+        } else {
+          const double nr = sqrt(al.re * al.re + al.im * al.im + tail);
+          const double bt = al.re >= 0.0 ? -nr : nr;
+          tau = mk<double>((bt - al.re) / bt, -al.im / bt);
+          const c128 dnm = mk<double>(al.re - bt, al.im);
+          const double dd = dnm.re * dnm.re + dnm.im * dnm.im;
+          sc = mk<double>(dnm.re / dd, -dnm.im / dd);
+        }
+        s_tau = tau;
+        s_sc = sc;
+        if (b == 0) {
+          // sequential swap semantics: the winner's current position p is swapped with j
+          const int p = a.pos_of[win], cj = a.col_at[j];
+          a.piv_seq[j] = p;
+          a.col_at[p] = cj;
+          a.pos_of[cj] = p;
+          a.col_at[j] = win;
+          a.pos_of[win] = j;
+        }
+      }
+    }
+    __syncthreads();
+    const T sc = ccast<R>(s_sc), ctau = cconj(ccast<R>(s_tau));
+    for (int r = j + 1 + tid; r < l; r += SKT) xw[r] = xw[r] * sc;  // v (v_j = 1 implicit)
+    if (win >= c0 && win < c1 && tid == 0) nrm[win - c0] = -1.0;    // consumed
+    __syncthreads();
+    if (!(s_tau.re == 0.0 && s_tau.im == 0.0)) {
+      for (int c = warp; c < nl; c += SKW) {
+        if (nrm[c] < 0.0) continue;
+        T* y = ys + c * l;
+        const T top = y[j];
+        T d = mk<R>(0, 0);
+        for (int r = j + 1 + lane; r < l; r += 32) cfma_conj(d, xw[r], y[r]);
+        d.re = warp_sum(d.re);
+        d.im = warp_sum(d.im);
+        d = d + top;
+        const T f = ctau * d;
+        __syncwarp();
+        if (lane == 0) y[j] = top - f;
+        for (int r = j + 1 + lane; r < l; r += 32) y[r] = y[r] - xw[r] * f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+static size_t sketch_piv_smem(int l, int nl) {
+  return (size_t)l * nl * sizeof(T) + (size_t)((nl + 1) & ~1) * 8 + (size_t)l * sizeof(T);
+}
+
+// Launch sketch_pivots_kernel for the l x nc sketch Y (pub: 2 G (l + 2) elements of
+// scratch, maps: 2 nc ints).
+template <typename T>
+static cudaError_t launch_sketch_pivots(const T* Y, int64_t ldy, int l, int nc, int kb, int* piv_seq, int* maps,
+                                        T* pub, int64_t pub_cap, unsigned* bar, int* err, unsigned barrier_extra,
+                                        unsigned long long timeout_ns, cudaStream_t s) {
+  static PerDevice once;
+  cudaError_t attr = cudaSuccess;
+  once.get([&attr]() -> long long {
+    attr = cudaFuncSetAttribute(sketch_pivots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmem);
+    return attr == cudaSuccess ? 1 : -1;
+  });
+  if (attr != cudaSuccess) return attr;
+  // about 48 columns per CTA, one CTA per SM at most (co-resident), shared memory permitting
+  int G = std::max(1, std::min(num_sms(), (nc + 47) / 48));
+  while (G < num_sms() && sketch_piv_smem<T>(l, (nc + G - 1) / G) > (size_t)kPanelSmem) ++G;
+  const size_t smem = sketch_piv_smem<T>(l, (nc + G - 1) / G);
+  if (smem > (size_t)kPanelSmem || 2 * (int64_t)G * (l + 2) > pub_cap) return cudaErrorInvalidConfiguration;
+  SketchPivArgs<T> a;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.l = l;
+  a.nc = nc;
+  a.kb = kb;
+  a.piv_seq = piv_seq;
+  a.col_at = maps;
+  a.pos_of = maps + nc;
+  a.pub = pub;
+  a.bar = bar;
+  a.err = err;
+  a.expected = (unsigned)G + barrier_extra;
+  a.timeout_ns = timeout_ns;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)sketch_pivots_kernel<T>, dim3(G), dim3(SKT), args, smem, s);
+}
+
 template <typename T>
 cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
   using R = typename real_of<T>::type;
@@ -1779,8 +2026,6 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
   int maxb = 1;
   CK(panel_setup<T>(maxb));
   const int gcap = std::max(1, std::min(p.G > 0 ? p.G : maxb, maxb));
-  // the sketch panel is short (l rows): a few CTAs keep its grid barriers cheap
-  const int gsk = std::max(1, std::min(gcap, 32));
   const int npanels = (k + nb - 1) / nb;
   CK(cudaMemsetAsync(p.Tfac, 0, sizeof(T) * (size_t)npanels * nb * nb, s));
   // Y = Omega W
@@ -1815,31 +2060,21 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
     const int kb = std::min(nb, k - j0);
     const int J1 = j0 + kb;
     const int nr = n - j0;
-    // a. the block's pivots: kb steps of the pivoted panel on a copy of the sketch's
-    //    remaining columns, which records the position taken at each step
-    hook_before(hooks, K(MPS_KCLASS_PANEL), (double)l * nr * kb * sizeof(T), 8.0 * l * nr * kb);
-    CK(cudaMemcpyAsync(p.Yw, p.Ys + (int64_t)j0 * ldy, sizeof(T) * (size_t)ldy * nr, cudaMemcpyDeviceToDevice, s));
-    iota_kernel<<<(nr + 255) / 256, 256, 0, s>>>(p.sk_jpvt, nr);
+    // a. the block's pivots from the sketch's remaining columns (sketch_pivots_kernel),
+    //    then the same column swaps on W, on the sketch and on jpvt
+    hook_before(hooks, K(MPS_KCLASS_PANEL), (double)l * nr * sizeof(T), 8.0 * l * nr * kb);
+    CK(launch_sketch_pivots<T>(p.Ys + (int64_t)j0 * ldy, ldy, l, nr, kb, p.piv_seq, reinterpret_cast<int*>(p.vn1),
+                               p.SK, p.sk_cap, p.bar, p.err, p.barrier_extra, p.timeout_ns, s));
+    apply_swaps_kernel<T><<<std::max(1, std::min(1024, (m + 255) / 256)), 256, 0, s>>>(p.W, p.ldw, m, j0, p.piv_seq,
+                                                                                      kb, p.jpvt);
     CK(cudaGetLastError());
-    col_norms_kernel<T><<<(nr + 7) / 8, 256, 0, s>>>(p.Yw, ldy, l, 0, 0, nr, p.vn1, p.vn2);
+    apply_swaps_kernel<T><<<1, 256, 0, s>>>(p.Ys, ldy, l, j0, p.piv_seq, kb, nullptr);
     CK(cudaGetLastError());
+    hook_after(hooks, K(MPS_KCLASS_PANEL), 3);
     PanelArgs<T> a;
-    a.W = p.Yw;
-    a.ldw = ldy;
-    a.m = l;
-    a.n = nr;
-    a.j0 = 0;
-    a.kb = kb;
-    a.nend = nr;
-    a.nb = nb;
-    a.pivot = 1;
     a.F = p.F;
     a.vn1 = p.vn1;
     a.vn2 = p.vn2;
-    a.jpvt = p.sk_jpvt;
-    a.tau = p.sk_tau;
-    a.Tp = nullptr;
-    a.Wg = p.sk_Wg;
     a.red_norm = p.red_norm;
     a.red_w = reinterpret_cast<T*>(p.red_w);
     a.red_argv = reinterpret_cast<long long*>(p.red_argv);
@@ -1849,15 +2084,8 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
     a.err = p.err;
     a.timeout_ns = p.timeout_ns;
     a.flag_tol = p.flag_tol;
-    a.piv_seq = p.piv_seq;
-    CK(launch_panel<T>(a, p.barrier_extra, gsk, false, s));
-    // the same column swaps on W, on the sketch and on jpvt
-    apply_swaps_kernel<T><<<std::max(1, std::min(1024, (m + 255) / 256)), 256, 0, s>>>(p.W, p.ldw, m, j0, p.piv_seq,
-                                                                                      kb, p.jpvt);
-    CK(cudaGetLastError());
-    apply_swaps_kernel<T><<<1, 256, 0, s>>>(p.Ys, ldy, l, j0, p.piv_seq, kb, nullptr);
-    CK(cudaGetLastError());
-    hook_after(hooks, K(MPS_KCLASS_PANEL), 5);
+    a.nb = nb;
+    a.kb = kb;
     // b. the block without pivoting (as a centre move's panel)
     PanelArgs<T> b = a;
     b.W = p.W;
