@@ -7,22 +7,26 @@
 //
 // Precision: each FP32 component x is split into big = tf32(x) (round to
 // nearest) and small = x - big; a real product is big*big + big*small +
-// small*big with FP32 accumulation ("3xTF32"), which keeps FP32-level
-// accuracy on the tensor cores.  A complex product is four real ones, so one
-// K-step issues 12 MMAs: re += ArBr - AiBi, im += ArBi + AiBr (the minus via the
-// instruction's negate-A bit).
+// small*big ("3xTF32"), which keeps FP32-level products on the tensor cores.  A
+// complex product is four real ones, so one K-step of 8 issues 12 MMAs:
+// re += ArBr - AiBi, im += ArBi + AiBr (the minus via the instruction's
+// negate-A bit).  The tensor cores' FP32 accumulation does not round to nearest,
+// and over a long K its error grows with K; so the MMAs of every kPromoteKs
+// K-steps go into a fresh TMEM accumulator (two buffers, alternating) that
+// accumulator warps read and add, rounding to nearest, into FP32 registers while
+// the MMAs go on into the other buffer.  The error then stays that of FP32 sums.
 //
-// CTA = 5 warps.  Warps 0-3 convert operand tiles (any layout, optional
+// CTA = 9 warps.  Warps 0-3 convert operand tiles (any layout, optional
 // conjugation / triangular mask) from global memory into the 128-byte-swizzled
 // K-major shared-memory layout the MMA reads: four planar parts (re big, im
-// big, re small, im small) per operand.  Warp 4 owns the TMEM allocation and
-// one of its threads issues the MMAs.  A two-stage mbarrier pipeline
-// overlaps conversion with the MMAs; every wait is bounded and records
-// DEV_ERR_TIMEOUT in the device error word on expiry.  The epilogue (warps
-// 0-3, one accumulator row per thread) reads TMEM with tcgen05.ld.
+// big, re small, im small) per operand.  Warp 4 owns the TMEM allocation and one
+// of its threads issues the MMAs.  Warps 5-8 hold the register accumulators (one
+// row each per thread) and run the epilogue.  Two-stage mbarrier pipeline for the
+// operands, two TMEM buffers for the partial sums; every wait is bounded and
+// records DEV_ERR_TIMEOUT in the device error word on expiry.
 //
-// Tile: 128 rows (M) x 64 complex columns (N) x 32 K per stage.  TMEM: real
-// parts in columns [0, 64), imaginary parts in [64, 128).
+// Tile: 128 rows (M) x 64 complex columns (N) x 32 K per stage.  TMEM buffer q:
+// real parts in columns [128 q, 128 q + 64), imaginary parts in the next 64.
 #include <algorithm>
 #include <cstring>
 
@@ -37,9 +41,11 @@ constexpr int A_PART = TM * TK * 4;            // bytes of one planar part of an
 constexpr int B_PART = TN * TK * 4;            // 8 KB
 constexpr int STAGE = 4 * A_PART + 4 * B_PART; // 96 KB
 constexpr int NSTAGE = 2;
-constexpr int TC_THREADS = 160;
+constexpr int TC_THREADS = 288;
 constexpr int TC_SMEM = NSTAGE * STAGE + 1024;  // + alignment slack
-constexpr int TMEM_COLS = 128;
+constexpr int TMEM_COLS = 256;                  // two accumulator buffers of 2 x TN columns
+constexpr int kPromoteKs = 1;                   // K-steps of 8 per TMEM partial sum
+constexpr int kBlocksPerStage = (TK / 8) / kPromoteKs;
 
 struct TcOperand {
   const c64* p;
@@ -189,7 +195,7 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long bar_full[NSTAGE], bar_empty[NSTAGE], bar_done;
+  __shared__ __align__(8) unsigned long long bar_full[NSTAGE], bar_empty[NSTAGE], acc_full[2], acc_empty[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_skip;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -200,13 +206,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tm = blockIdx.x, tn = blockIdx.y;
   const int nkb = (a.K + TK - 1) / TK;
+  const int nblk = nkb * kBlocksPerStage;  // TMEM partial sums of the whole K range
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(smem_u32(&bar_full[s]), 128);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_done), 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&acc_full[q]), 1);
+      mbar_init(smem_u32(&acc_empty[q]), 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 4) {
@@ -221,6 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   const uint32_t tmem = s_tmem;
 
   bool ok = true;
+  float accr[TN], acci[TN];  // accumulator warps: row (warp % 4) * 32 + lane, every column of the tile
   if (warp < 4) {
     // ---- converters
     for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -233,103 +244,131 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&bar_full[s]));
     }
-  } else if (lane == 0) {
-    // ---- MMA issuer
-    const uint32_t dre = tmem, dim = tmem + TN;
-    const uint32_t id_pos = idesc_tf32(0), id_neg = idesc_tf32(1);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb & 1;
-      if (!mbar_wait(smem_u32(&bar_full[s]), (kb >> 1) & 1, a.err, a.timeout_ns)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(sm + s * STAGE);
-      for (int ks = 0; ks < TK / 8; ++ks) {
-        const uint32_t ko = ks * 32;  // 8 tf32 = 32 bytes along K inside the swizzle atom
-        const uint64_t arb = sdesc(st + 0 * A_PART + ko), aib = sdesc(st + 1 * A_PART + ko);
-        const uint64_t ars = sdesc(st + 2 * A_PART + ko), ais = sdesc(st + 3 * A_PART + ko);
-        const uint32_t bst = st + 4 * A_PART;
-        const uint64_t brb = sdesc(bst + 0 * B_PART + ko), bib = sdesc(bst + 1 * B_PART + ko);
-        const uint64_t brs = sdesc(bst + 2 * B_PART + ko), bis = sdesc(bst + 3 * B_PART + ko);
-        const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
-        // re += Ar Br - Ai Bi
-        umma(dre, arb, brb, id_pos, first);
-        umma(dre, arb, brs, id_pos, 1);
-        umma(dre, ars, brb, id_pos, 1);
-        umma(dre, aib, bib, id_neg, 1);
-        umma(dre, aib, bis, id_neg, 1);
-        umma(dre, ais, bib, id_neg, 1);
-        // im += Ar Bi + Ai Br
-        umma(dim, arb, bib, id_pos, first);
-        umma(dim, arb, bis, id_pos, 1);
-        umma(dim, ars, bib, id_pos, 1);
-        umma(dim, aib, brb, id_pos, 1);
-        umma(dim, aib, brs, id_pos, 1);
-        umma(dim, ais, brb, id_pos, 1);
+  } else if (warp == 4) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t id_pos = idesc_tf32(0), id_neg = idesc_tf32(1);
+      int blk = 0;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb & 1;
+        if (!mbar_wait(smem_u32(&bar_full[s]), (kb >> 1) & 1, a.err, a.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(sm + s * STAGE);
+        for (int ks = 0; ks < TK / 8 && ok; ++ks) {
+          const int q = blk & 1;
+          const bool opens = ks % kPromoteKs == 0;
+          if (opens && blk >= 2) {
+            // the accumulator warps have read this buffer's previous partial sum
+            if (!mbar_wait(smem_u32(&acc_empty[q]), ((blk >> 1) - 1) & 1, a.err, a.timeout_ns)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          const uint32_t dre = tmem + q * 2 * TN, dim = dre + TN;
+          const uint32_t ko = ks * 32;  // 8 tf32 = 32 bytes along K inside the swizzle atom
+          const uint64_t arb = sdesc(st + 0 * A_PART + ko), aib = sdesc(st + 1 * A_PART + ko);
+          const uint64_t ars = sdesc(st + 2 * A_PART + ko), ais = sdesc(st + 3 * A_PART + ko);
+          const uint32_t bst = st + 4 * A_PART;
+          const uint64_t brb = sdesc(bst + 0 * B_PART + ko), bib = sdesc(bst + 1 * B_PART + ko);
+          const uint64_t brs = sdesc(bst + 2 * B_PART + ko), bis = sdesc(bst + 3 * B_PART + ko);
+          const uint32_t first = opens ? 0u : 1u;
+          // re += Ar Br - Ai Bi
+          umma(dre, arb, brb, id_pos, first);
+          umma(dre, arb, brs, id_pos, 1);
+          umma(dre, ars, brb, id_pos, 1);
+          umma(dre, aib, bib, id_neg, 1);
+          umma(dre, aib, bis, id_neg, 1);
+          umma(dre, ais, bib, id_neg, 1);
+          // im += Ar Bi + Ai Br
+          umma(dim, arb, bib, id_pos, first);
+          umma(dim, arb, bis, id_pos, 1);
+          umma(dim, ars, bib, id_pos, 1);
+          umma(dim, aib, brb, id_pos, 1);
+          umma(dim, aib, brs, id_pos, 1);
+          umma(dim, ais, brb, id_pos, 1);
+          if (ks % kPromoteKs == kPromoteKs - 1) {
+            umma_commit(smem_u32(&acc_full[q]));  // fires when this partial sum is complete
+            ++blk;
+          }
+        }
+        umma_commit(smem_u32(&bar_empty[s]));
       }
-      umma_commit(smem_u32(&bar_empty[s]));
     }
-    umma_commit(smem_u32(&bar_done));  // fires once every MMA issued so far has completed
-  }
-
-  // ---- epilogue: warps 0-3, thread = accumulator row
-  if (warp < 4) {
-    const bool ready = mbar_wait(smem_u32(&bar_done), 0, a.err, a.timeout_ns);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool store = ready && ld_relaxed_i32(a.err) == DEV_OK;
-    const int rloc = 32 * warp + lane;
-    const int i = tm * TM + rloc;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-    if (!a.theta) {
+  } else {
+    // ---- accumulator warps: add every TMEM partial sum into registers (round to nearest)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      accr[c] = 0.f;
+      acci[c] = 0.f;
+    }
+    const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int blk = 0; blk < nblk; ++blk) {
+      const int q = blk & 1;
+      if (!mbar_wait(smem_u32(&acc_full[q]), (blk >> 1) & 1, a.err, a.timeout_ns)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
       for (int c0 = 0; c0 < TN; c0 += 16) {
         float re[16], im[16];
-        tmem_ld16(trow + c0, re);
-        tmem_ld16(trow + TN + c0, im);
+        tmem_ld16(trow + q * 2 * TN + c0, re);
+        tmem_ld16(trow + q * 2 * TN + TN + c0, im);
         tmem_wait_ld();
-        if (store && i < a.M) {
-          const bool bz = (a.beta.re == 0.f && a.beta.im == 0.f);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int j = tn * TN + c0 + q;
-            if (j < a.N) {
-              c64* cp = a.C + i + (int64_t)j * a.ldc;
-              c64 v = a.alpha * mk<float>(re[q], im[q]);
-              if (!bz) v = v + a.beta * (*cp);
-              *cp = v;
-            }
+        for (int c = 0; c < 16; ++c) {
+          accr[c0 + c] += re[c];
+          acci[c0 + c] += im[c];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&acc_empty[q]));
+    }
+    // ---- epilogue from the registers
+    const bool store = ok && ld_relaxed_i32(a.err) == DEV_OK;
+    const int i = tm * TM + 32 * (warp & 3) + lane;
+    if (!a.theta) {
+      if (store && i < a.M) {
+        const bool bz = (a.beta.re == 0.f && a.beta.im == 0.f);
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {  // fully unrolled: the accumulators stay in registers
+          const int j = tn * TN + c;
+          if (j < a.N) {
+            c64* cp = a.C + i + (int64_t)j * a.ldc;
+            c64 v = a.alpha * mk<float>(accr[c], acci[c]);
+            if (!bz) v = v + a.beta * (*cp);
+            *cp = v;
           }
         }
       }
     } else {
-      // theta: row i = (l, c) = 2l + c, TMEM column u = (d, r) = 32d + (r - 32 tn)
+      // theta: row i = (l, c) = 2l + c, column u = (d, r) = 32d + (r - 32 tn)
       const int ca = i & 1, l = i >> 1;
-      for (int h = 0; h < 32; h += 16) {
-        float x0r[16], x0i[16], x1r[16], x1i[16];  // d = 0 and d = 1 for 16 values of r
-        tmem_ld16(trow + h, x0r);
-        tmem_ld16(trow + TN + h, x0i);
-        tmem_ld16(trow + 32 + h, x1r);
-        tmem_ld16(trow + TN + 32 + h, x1i);
-        tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          // X[(l, c'), (d, r)] for both c' (own row and partner row i^1)
-          c64 own0 = mk<float>(x0r[q], x0i[q]), own1 = mk<float>(x1r[q], x1i[q]);
-          c64 oth0, oth1;
-          oth0.re = __shfl_xor_sync(0xffffffffu, own0.re, 1);
-          oth0.im = __shfl_xor_sync(0xffffffffu, own0.im, 1);
-          oth1.re = __shfl_xor_sync(0xffffffffu, own1.re, 1);
-          oth1.im = __shfl_xor_sync(0xffffffffu, own1.im, 1);
-          const c64 xc0d0 = ca ? oth0 : own0, xc0d1 = ca ? oth1 : own1;
-          const c64 xc1d0 = ca ? own0 : oth0, xc1d1 = ca ? own1 : oth1;
-          const int r = 32 * tn + h + q;
-          if (store && l < a.cl && r < a.cr) {
+      for (int q = 0; q < 32; ++q) {
+        // X[(l, c'), (d, r)] for both c' (own row and partner row i^1)
+        const c64 own0 = mk<float>(accr[q], acci[q]), own1 = mk<float>(accr[32 + q], acci[32 + q]);
+        c64 oth0, oth1;
+        oth0.re = __shfl_xor_sync(0xffffffffu, own0.re, 1);
+        oth0.im = __shfl_xor_sync(0xffffffffu, own0.im, 1);
+        oth1.re = __shfl_xor_sync(0xffffffffu, own1.re, 1);
+        oth1.im = __shfl_xor_sync(0xffffffffu, own1.im, 1);
+        const c64 xc0d0 = ca ? oth0 : own0, xc0d1 = ca ? oth1 : own1;
+        const c64 xc1d0 = ca ? own0 : oth0, xc1d1 = ca ? own1 : oth1;
+        const int r = 32 * tn + q;
+        if (store && l < a.cl && r < a.cr) {
 #pragma unroll
-            for (int bb = 0; bb < 2; ++bb) {
-              const c64* gr = a.g + (2 * ca + bb) * 4;
-              c64 v = gr[0] * xc0d0;
-              cfma(v, gr[1], xc0d1);
-              cfma(v, gr[2], xc1d0);
-              cfma(v, gr[3], xc1d1);
-              a.W[(int64_t)(bb * a.cr + r) * a.ldw + i] = v;
-            }
+          for (int bb = 0; bb < 2; ++bb) {
+            const c64* gr = a.g + (2 * ca + bb) * 4;
+            c64 v = gr[0] * xc0d0;
+            cfma(v, gr[1], xc0d1);
+            cfma(v, gr[2], xc1d0);
+            cfma(v, gr[3], xc1d1);
+            a.W[(int64_t)(bb * a.cr + r) * a.ldw + i] = v;
           }
         }
       }
@@ -341,7 +380,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  (void)ok;
 }
 
 PerDevice g_tc_init;  // kernel attribute set once per device
