@@ -206,7 +206,8 @@ def ours(args):
 
     # --- mixed path, timed with per-kernel-class CUDA events
     tr = {"truncation": args.truncation}
-    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, profile=True, device=local, **tr)
+    tc = {"tensor_cores": True} if args.tensor_cores else {}
+    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, profile=True, device=local, **tr, **tc)
     m.set_sites([s.astype(np.complex64) for s in sites], centre=i)
     with ClockSampler(local) as clk:
         if ws > 1:
@@ -232,7 +233,7 @@ def ours(args):
 
         # --- deviation of the mixed path from the FP64 path: a mixed state run through
         # exactly the FP64 steps, compared result by result
-        mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local, **tr)
+        mm = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local, **tr, **tc)
         mm.set_sites([s.astype(np.complex64) for s in sites], centre=i)
         for stp in seq[:args.fp64_warmup + args.fp64_steps]:
             do_step_at(mm, stp, i)
@@ -404,7 +405,8 @@ def e2e_run(args, sites, seq, n, chi, i, sptr, local, torch, np):
     move, gate or SWAP, split) and reads the two new sites back."""
     from paper_2505_06119_gb300 import MPS
 
-    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local, truncation=args.truncation)
+    m = MPS(n, chi, precision="mixed", policy="canon", stream=sptr, device=local, truncation=args.truncation,
+            tensor_cores=args.tensor_cores)
     m.set_sites([s.astype(np.complex64) for s in sites], centre=i)
     do_step(m, seq[0], i)
     shape_a = (chi, 2, chi)
@@ -924,6 +926,8 @@ def main():
     ap.add_argument("--chi", type=int, default=CHI)
     ap.add_argument("--fp64-steps", type=int, default=19)
     ap.add_argument("--amp-samples", type=int, default=64)
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="mixed path: long complex products on the tcgen05 tensor cores (3xTF32)")
     ap.add_argument("--truncation", default="qrcp", choices=["qrcp", "rqrcp"],
                     help="split of the gate workload: the deterministic pivoted QR (the metric's) or "
                          "randomized pivoting")

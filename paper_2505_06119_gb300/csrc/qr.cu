@@ -1991,9 +1991,11 @@ static cudaError_t launch_sketch_pivots(const T* Y, int64_t ldy, int l, int nc, 
     return attr == cudaSuccess ? 1 : -1;
   });
   if (attr != cudaSuccess) return attr;
-  // about 48 columns per CTA, one CTA per SM at most (co-resident), shared memory permitting
-  int G = std::max(1, std::min(num_sms(), (nc + 47) / 48));
-  while (G < num_sms() && sketch_piv_smem<T>(l, (nc + G - 1) / G) > (size_t)kPanelSmem) ++G;
+  // about 512 columns per CTA: the per-step work is a few microseconds of shared-memory
+  // arithmetic, so few CTAs keep the grid barrier and the winner scan short; more CTAs
+  // only where the columns do not fit one CTA's shared memory (one CTA per SM at most)
+  int G = std::max(1, std::min(num_sms(), (nc + 511) / 512));
+  while (G < num_sms() && sketch_piv_smem<T>(l, (nc + G - 1) / G) > (size_t)(160 * 1024)) ++G;
   const size_t smem = sketch_piv_smem<T>(l, (nc + G - 1) / G);
   if (smem > (size_t)kPanelSmem || 2 * (int64_t)G * (l + 2) > pub_cap) return cudaErrorInvalidConfiguration;
   SketchPivArgs<T> a;
