@@ -156,20 +156,28 @@ class ClockSampler:
 # dram bytes / algorithmic bytes of the captured launch.  Traffic scales with the
 # algorithmic bytes (both are sums over the trailing block), so a launch's traffic is
 # this ratio times its algorithmic bytes.  Valid only for the kernel source it was
-# measured on (sha256 of csrc/qr.cu); otherwise reported as null.
-PANEL_NCU = {"qr_cu_sha256": "3b4f929abb7c11b6968f3c418be998f909aa72a659af441ccb9a3e4952cae2db",
-             "dram_over_algorithmic": 0.9896}
+# measured on (sha256 of the qr_panel_kernel definition in csrc/qr.cu); otherwise null.
+PANEL_NCU = {"kernel_sha256": None, "dram_over_algorithmic": None}
+
+
+def panel_kernel_source():
+    """The text of qr_panel_kernel's definition in csrc/qr.cu (up to the section on the
+    unpivoted cluster panel that follows it)."""
+    with open(os.path.join(ROOT, "paper_2505_06119_gb300", "csrc", "qr.cu")) as f:
+        src = f.read()
+    start = src.index("__global__ void __launch_bounds__(PNT, 1) qr_panel_kernel")
+    end = src.index("// Unpivoted panel on one thread-block cluster", start)
+    return src[start:end]
 
 
 def panel_traffic(alg_bytes_per_launch):
     import hashlib
 
     try:
-        with open(os.path.join(ROOT, "paper_2505_06119_gb300", "csrc", "qr.cu"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = hashlib.sha256(panel_kernel_source().encode()).hexdigest()
     except Exception:
         return None
-    if sha != PANEL_NCU["qr_cu_sha256"]:
+    if PANEL_NCU["kernel_sha256"] is None or sha != PANEL_NCU["kernel_sha256"]:
         return None
     return PANEL_NCU["dram_over_algorithmic"] * alg_bytes_per_launch
 

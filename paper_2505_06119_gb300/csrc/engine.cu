@@ -167,8 +167,9 @@ struct Knobs {
 
 template <typename T>
 SmallGate<T> small_item(int cl, int cm, int cr, int k, const T* A, const T* B, const T* g, T* Aout, T* Bout,
-                        double* disc, double* disc_total, int* jpvt_out) {
+                        double* disc, double* disc_total, int* jpvt_out, const T* gdev = nullptr) {
   SmallGate<T> it;
+  it.gdev = gdev;
   it.A = A;
   it.B = B;
   it.Aout = Aout;
@@ -241,17 +242,17 @@ void gate_to_T(const mps_c128* g, int count, T* out) {
 // theta contraction + gate -> truncated pivoted QR -> Q formation -> split.
 template <typename T>
 cudaError_t theta_step(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, const T* A, const T* B, const T* g,
-                       cudaStream_t s, LaunchHooks* hk) {
+                       cudaStream_t s, LaunchHooks* hk, const T* gdev = nullptr) {
   const int m = 2 * cl, n = 2 * cr;
   hook_before(hk, MPS_KCLASS_THETA, ((double)m * cm + (double)cm * n + (double)m * n) * sizeof(T),
               8.0 * m * n * cm + 32.0 * m * n);
   if constexpr (std::is_same<T, c64>::value) {
     if (kn.use_tc)
-      CKE(tc_theta(cl, cm, cr, A, B, g, w.W, w.ldw, w.err, kn.timeout_ns, s));
+      CKE(tc_theta(cl, cm, cr, A, B, g, w.W, w.ldw, w.err, kn.timeout_ns, s, gdev));
     else
-      CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s));
+      CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s, gdev));
   } else {
-    CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s));
+    CKE(theta_gemm_simt<T>(cl, cm, cr, A, B, g, w.W, w.ldw, s, gdev));
   }
   hook_after(hk, MPS_KCLASS_THETA, 1);
   return cudaSuccess;
@@ -265,21 +266,21 @@ void plan_sketch(QrPlan<T>& p, const SketchRef& sk);
 template <typename T>
 cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int cr, int chi, const T* A, const T* B,
                           const T* g, T* Aout, T* Bout, double* disc_slot, double* disc_total, cudaStream_t s,
-                          LaunchHooks* hk, const SketchRef* sk = nullptr) {
+                          LaunchHooks* hk, const SketchRef* sk = nullptr, const T* gdev = nullptr) {
   const int m = 2 * cl, n = 2 * cr;
   const int k = std::min(std::min(m, n), chi);
   if (!sk && kn.small && small_gate_fits(cl, cm, cr)) {
     // the whole split in one CTA
     SmallBatch<T> b;
     b.count = 1;
-    b.item[0] = small_item<T>(cl, cm, cr, k, A, B, g, Aout, Bout, disc_slot, disc_total, w.jpvt);
+    b.item[0] = small_item<T>(cl, cm, cr, k, A, B, g, Aout, Bout, disc_slot, disc_total, w.jpvt, gdev);
     hook_before(hk, MPS_KCLASS_PANEL, ((double)m * cm + (double)cm * n + 2.0 * (m + n) * k) * sizeof(T),
                 8.0 * m * n * cm + 16.0 * m * n * k + 8.0 * m * k * k);
     CKE(small_gate_launch<T>(b, s));
     hook_after(hk, MPS_KCLASS_PANEL, 1);
     return cudaSuccess;
   }
-  CKE(theta_step<T>(w, kn, cl, cm, cr, A, B, g, s, hk));
+  CKE(theta_step<T>(w, kn, cl, cm, cr, A, B, g, s, hk, gdev));
   QrPlan<T> p = make_plan<T>(w, kn, m, n, k, 1, disc_slot, disc_total);
   if (sk) plan_sketch<T>(p, *sk);
   CKE(qr_factor<T>(p, s, hk));
@@ -487,6 +488,9 @@ struct Lane {
 struct GraphSlot {
   std::string key;  // layer shape: precision, bond cap, (site, bond dims) per gate
   cudaGraphExec_t exec = nullptr;
+  char* staging = nullptr;   // pinned host copy of the layer's parameters, read by the graph's first node
+  size_t staging_bytes = 0;
+  cudaEvent_t done = nullptr;  // the graph's last launch has finished (staging reusable)
   long long launches = 0;
 };
 
@@ -538,6 +542,11 @@ struct mps_s {
   long long layer_calls = 0;
   long long graph_launches = 0;  // layers run as a graph launch
   std::vector<GraphSlot> graph_cache;
+  // device parameters of a replayed layer: [0] the split counter of its first gate,
+  // from byte 16 the gates in the data type (16 entries each); per-gate discarded
+  // weights land in ldisc and are filed into the log by the graph's last kernel
+  char* layer_dev = nullptr;
+  double* ldisc = nullptr;
   // autotuning (MPS_FLAG_AUTOTUNE): scratch outputs of the timed candidate splits
   bool tune = false;
   char* tune_ws = nullptr;
@@ -593,8 +602,11 @@ void release(mps_t h) {
     if (ln.done) cudaEventDestroy(ln.done);
   }
   h->lanes.clear();
-  for (GraphSlot& g : h->graph_cache)
+  for (GraphSlot& g : h->graph_cache) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.done) cudaEventDestroy(g.done);
+    if (g.staging) cudaFreeHost(g.staging);
+  }
   h->graph_cache.clear();
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   h->ev_fork = nullptr;
@@ -1135,42 +1147,31 @@ int lanes_ready(mps_t h) {
     // the allocation is stream-ordered on the handle's stream; the lane starts after it
     CUTRY(h, cudaMemsetAsync(ln.ws + ln.L.bar, 0, 16, h->stream), "layer lanes");
   }
+  // parameters of replayed layers (at most n - 1 gates)
+  h->layer_dev = (char*)dev_alloc(h, 16 + (size_t)h->n * 16 * h->esz);
+  h->ldisc = (double*)dev_alloc(h, sizeof(double) * (size_t)h->n);
+  if (!h->layer_dev || !h->ldisc) return fail(h, MPS_E_NOMEM, "layer parameters");
   CUTRY(h, cudaStreamSynchronize(h->stream), "layer lanes");
   return MPS_OK;
 }
 
-// Launch a captured layer graph through the handle's cache of executable graphs
-// (one per layer shape, at most kGraphCache): update the cached one in place when
-// the topology matches, else instantiate anew.
-constexpr size_t kGraphCache = 16;
-
-cudaError_t graph_launch(mps_t h, const std::string& key, cudaGraph_t graph) {
-  GraphSlot* slot = nullptr;
-  for (GraphSlot& g : h->graph_cache)
-    if (g.key == key) slot = &g;
-  if (slot) {
-    cudaGraphExecUpdateResultInfo info;
-    if (cudaGraphExecUpdate(slot->exec, graph, &info) != cudaSuccess) {
-      cudaGetLastError();
-      cudaGraphExecDestroy(slot->exec);
-      slot->exec = nullptr;
-      CKE(cudaGraphInstantiate(&slot->exec, graph, 0));
+// last node of a replayed layer: file the per-gate discarded weights into the log
+// at the split counter held in the parameter block, and add them to the total in
+// gate order (the same sum as add_slots_kernel's)
+__global__ void file_disc_kernel(const double* ldisc, int count, const long long* first, double* log,
+                                 double* total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const long long f = *first;
+    double t = *total;
+    for (int j = 0; j < count; ++j) {
+      log[(f + j) % kDiscLog] = ldisc[j];
+      t += ldisc[j];
     }
-  } else {
-    if (h->graph_cache.size() >= kGraphCache) {
-      cudaGraphExecDestroy(h->graph_cache.front().exec);
-      h->graph_cache.erase(h->graph_cache.begin());
-    }
-    GraphSlot g;
-    g.key = key;
-    CKE(cudaGraphInstantiate(&g.exec, graph, 0));
-    h->graph_cache.push_back(g);
-    slot = &h->graph_cache.back();
+    *total = t;
   }
-  slot->launches++;
-  h->graph_launches++;
-  return cudaGraphLaunch(slot->exec, h->stream);
 }
+
+constexpr size_t kGraphCache = 16;  // executable layer graphs kept per handle
 
 template <typename T>
 int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi) {
@@ -1222,9 +1223,17 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
   // every panel step are those of a full grid, so results do not change.
   const int share = num_sms() / std::max(1, std::min<int>((int)small.size(), kLanes));
   // Every launch of the layer, in order: the lanes' gates, the grouped launches of
-  // the small gates, the large gates on the handle's stream, the join and the sum
-  // of the discarded weights.  Returns the first failing call's error.
-  auto issue = [&]() -> cudaError_t {
+  // the small gates, the large gates on the handle's stream, the join and the
+  // filing of the discarded weights.  With `staging` (a replayable layer, captured
+  // into a CUDA graph) the gates are read from the device parameter block, which the
+  // first node copies from the pinned staging buffer, and the discarded weights go
+  // through ldisc.  Returns the first failing call's error.
+  auto issue = [&](const char* staging, size_t staging_bytes) -> cudaError_t {
+    const bool rp = staging != nullptr;
+    const T* gbase = rp ? reinterpret_cast<const T*>(h->layer_dev + 16) : nullptr;
+    auto disc_of = [&](int j) { return rp ? h->ldisc + j : slot_of(j); };
+    auto gdev_of = [&](int j) { return rp ? gbase + 16 * j : nullptr; };
+    if (rp) CKE(cudaMemcpyAsync(h->layer_dev, staging, staging_bytes, cudaMemcpyHostToDevice, h->stream));
     CKE(cudaEventRecord(h->ev_fork, h->stream));
     std::vector<double> load(kLanes, 0.0);
     std::vector<char> used(kLanes, 0);
@@ -1244,7 +1253,8 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
       Knobs kl = kj[it.j];
       kl.G = std::min(kl.G, std::max((2 * it.cl + 127) / 128, share));
       CKE(two_site_core<T>(w, kl, it.cl, it.cm, it.cr, chi, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
-                           (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr, ln.stream, &h->prof.hooks));
+                           (T*)h->site[i], (T*)h->site[i + 1], disc_of(it.j), nullptr, ln.stream, &h->prof.hooks,
+                           nullptr, gdev_of(it.j)));
     }
     // the gates whose theta fits one CTA: one grouped launch per kSmallBatch of them
     for (size_t b0 = 0; b0 < tiny.size(); b0 += kSmallBatch) {
@@ -1256,7 +1266,8 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
         gate_to_T<T>(gates + 16 * it.j, 16, gt);
         const int i = sites[it.j];
         sb.item[q] = small_item<T>(it.cl, it.cm, it.cr, it.k, (const T*)h->site[i], (const T*)h->site[i + 1], gt,
-                                   (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr, nullptr);
+                                   (T*)h->site[i], (T*)h->site[i + 1], disc_of(it.j), nullptr, nullptr,
+                                   gdev_of(it.j));
       }
       CKE(small_gate_launch<T>(sb, h->stream));
     }
@@ -1265,22 +1276,28 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
       gate_to_T<T>(gates + 16 * it.j, 16, gt);
       const int i = sites[it.j];
       CKE(two_site_core<T>(views<T>(h), kj[it.j], it.cl, it.cm, it.cr, chi, (const T*)h->site[i],
-                           (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1], slot_of(it.j), nullptr,
-                           h->stream, &h->prof.hooks));
+                           (const T*)h->site[i + 1], gt, (T*)h->site[i], (T*)h->site[i + 1], disc_of(it.j), nullptr,
+                           h->stream, &h->prof.hooks, nullptr, gdev_of(it.j)));
     }
     for (int l = 0; l < kLanes; ++l) {
       if (!used[l]) continue;
       CKE(cudaEventRecord(h->lanes[l].done, h->lanes[l].stream));
       CKE(cudaStreamWaitEvent(h->stream, h->lanes[l].done, 0));
     }
-    add_slots_kernel<<<1, 32, 0, h->stream>>>(h->d_disclog, (int)(first % kDiscLog), count, h->d_scalar + 1);
+    if (rp)
+      file_disc_kernel<<<1, 32, 0, h->stream>>>(h->ldisc, count, reinterpret_cast<const long long*>(h->layer_dev),
+                                                h->d_disclog, h->d_scalar + 1);
+    else
+      add_slots_kernel<<<1, 32, 0, h->stream>>>(h->d_disclog, (int)(first % kDiscLog), count, h->d_scalar + 1);
     return cudaGetLastError();
   };
-  // After the first layer call (which sets every kernel up), a layer is captured
-  // into a CUDA graph and replayed: the graph of a layer of the same shape (sites,
-  // bond dims, bond cap) is updated in place with this layer's parameters (gates,
-  // discarded-weight slots) and launched as one unit.  If the stream cannot be
-  // captured, the layer is issued directly and graphs stay off for the handle.
+  // After the first layer call (which sets every kernel up), each layer shape
+  // (precision, bond cap, and per gate the site and its three bond dims) is
+  // captured once into a CUDA graph whose parameters (the gates and the split
+  // counter) live in device memory; a layer of a known shape is then one graph
+  // launch after its parameters are written to the pinned staging buffer that the
+  // graph's first node copies.  If the stream cannot be captured, the layer is
+  // issued directly and graphs stay off for the handle.
   bool done = false;
   if (h->graphs && h->layer_calls > 0) {
     std::string key = std::to_string(h->prec) + ":" + std::to_string(chi);
@@ -1289,24 +1306,67 @@ int layer_t(mps_t h, const int* sites, const mps_c128* gates, int count, int chi
       key += ";" + std::to_string(i) + "," + std::to_string(h->bond[i]) + "," + std::to_string(h->bond[i + 1]) + "," +
              std::to_string(h->bond[i + 2]);
     }
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      const cudaError_t ei = issue();
-      e = cudaStreamEndCapture(h->stream, &graph);
-      if (ei != cudaSuccess) e = ei;
+    GraphSlot* slot = nullptr;
+    for (GraphSlot& g : h->graph_cache)
+      if (g.key == key) slot = &g;
+    cudaError_t e = cudaSuccess;
+    if (!slot) {
+      GraphSlot g;
+      g.key = key;
+      g.staging_bytes = 16 + (size_t)count * 16 * sizeof(T);
+      cudaGraph_t graph = nullptr;
+      e = cudaMallocHost(&g.staging, g.staging_bytes);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t ei = issue(g.staging, g.staging_bytes);
+        e = cudaStreamEndCapture(h->stream, &graph);
+        if (ei != cudaSuccess) e = ei;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e == cudaSuccess) {
+        if (h->graph_cache.size() >= kGraphCache) {
+          GraphSlot& old = h->graph_cache.front();
+          cudaEventSynchronize(old.done);
+          cudaGraphExecDestroy(old.exec);
+          cudaEventDestroy(old.done);
+          cudaFreeHost(old.staging);
+          h->graph_cache.erase(h->graph_cache.begin());
+        }
+        h->graph_cache.push_back(g);
+        slot = &h->graph_cache.back();
+      } else {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.done) cudaEventDestroy(g.done);
+        if (g.staging) cudaFreeHost(g.staging);
+      }
     }
-    if (e == cudaSuccess && graph) e = graph_launch(h, key, graph);
-    if (graph) cudaGraphDestroy(graph);
-    if (e == cudaSuccess) {
-      done = true;
-    } else {
+    if (e == cudaSuccess && slot) {
+      // the previous launch of this graph has copied its parameters: the staging is free
+      e = cudaEventSynchronize(slot->done);
+      if (e == cudaSuccess) {
+        long long f = first;
+        memcpy(slot->staging, &f, sizeof f);
+        T* gs = reinterpret_cast<T*>(slot->staging + 16);
+        for (int j = 0; j < count; ++j) gate_to_T<T>(gates + 16 * j, 16, gs + 16 * j);
+        e = cudaGraphLaunch(slot->exec, h->stream);
+      }
+      if (e == cudaSuccess) {
+        // the layer is enqueued: never issue it a second time
+        slot->launches++;
+        h->graph_launches++;
+        done = true;
+        CUTRY(h, cudaEventRecord(slot->done, h->stream), "apply_layer: graph event");
+      }
+    }
+    if (!done) {
       cudaGetLastError();
       h->graphs = false;  // issue directly from now on
     }
   }
   if (!done) {
-    cudaError_t e = issue();
+    cudaError_t e = issue(nullptr, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "apply_layer");
   }
   h->layer_calls++;

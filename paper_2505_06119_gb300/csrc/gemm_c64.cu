@@ -50,6 +50,7 @@ constexpr int g_smem_bytes() {
 struct ThetaEpi {
   int cr;      // chi_r
   c64 g[16];   // gate, g[(2a+b)*4 + 2c+d]
+  const c64* gdev;  // the gate in device memory instead (layers replayed as CUDA graphs); NULL: g
   c64* W;      // theta, column-major, leading dimension ldw
   int64_t ldw;
 };
@@ -279,7 +280,10 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
-              for (int dd = 0; dd < 2; ++dd) cfma(s, te.g[(2 * a + b) * 4 + 2 * c + dd], X[c][dd]);
+              for (int dd = 0; dd < 2; ++dd) {
+                const int gi = (2 * a + b) * 4 + 2 * c + dd;
+                cfma(s, te.gdev ? te.gdev[gi] : te.g[gi], X[c][dd]);
+              }
             v[a] = s;
           }
           c64* dst = te.W + (int64_t)(b * te.cr + r) * te.ldw + 2 * l;
@@ -386,7 +390,7 @@ cudaError_t gemm_c64(const GemmDesc<c64>& d, cudaStream_t s) {
 }
 
 cudaError_t theta_c64(int cl, int cm, int cr, const c64* A, const c64* B, const c64* g16, c64* W, int64_t ldw,
-                      cudaStream_t s) {
+                      cudaStream_t s, const c64* gdev) {
   GemmDesc<c64> d;
   d.M = 2 * cl;
   d.N = 2 * cr;
@@ -402,6 +406,7 @@ cudaError_t theta_c64(int cl, int cm, int cr, const c64* A, const c64* B, const 
   ThetaEpi te;
   te.cr = cr;
   for (int q = 0; q < 16; ++q) te.g[q] = g16[q];
+  te.gdev = gdev;
   te.W = W;
   te.ldw = ldw;
   dim3 grid((d.M + 127) / 128, (cr + G_BN / 2 - 1) / (G_BN / 2), 1);

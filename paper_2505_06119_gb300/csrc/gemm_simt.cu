@@ -186,6 +186,7 @@ struct ThetaArgs {
   const T* A;
   const T* B;
   T g[16];
+  const T* gdev;  // the gate in device memory instead (layers replayed as CUDA graphs); NULL: g
   T* W;
   int64_t ldw;
 };
@@ -296,7 +297,10 @@ __global__ void __launch_bounds__(NT) theta_kernel(ThetaArgs<T> p) {
 #pragma unroll
           for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int dd = 0; dd < 2; ++dd) cfma(v, p.g[(2 * a + b) * 4 + 2 * c + dd], acc[li][ri][c][dd]);
+            for (int dd = 0; dd < 2; ++dd) {
+              const int gi = (2 * a + b) * 4 + 2 * c + dd;
+              cfma(v, p.gdev ? p.gdev[gi] : p.g[gi], acc[li][ri][c][dd]);
+            }
           p.W[(int64_t)(b * p.cr + r) * p.ldw + 2 * l + a] = v;
         }
     }
@@ -338,9 +342,9 @@ cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s) {
 
 template <typename T>
 cudaError_t theta_gemm_simt(int chi_l, int chi_m, int chi_r, const T* A, const T* B, const T* g16,
-                            T* W, int64_t ldw, cudaStream_t s) {
+                            T* W, int64_t ldw, cudaStream_t s, const T* gdev) {
   if constexpr (std::is_same<T, c64>::value) {
-    return theta_c64(chi_l, chi_m, chi_r, A, B, g16, W, ldw, s);
+    return theta_c64(chi_l, chi_m, chi_r, A, B, g16, W, ldw, s, gdev);
   } else {
     ThetaArgs<T> p;
     p.cl = chi_l;
@@ -349,6 +353,7 @@ cudaError_t theta_gemm_simt(int chi_l, int chi_m, int chi_r, const T* A, const T
     p.A = A;
     p.B = B;
     for (int i = 0; i < 16; ++i) p.g[i] = g16[i];
+    p.gdev = gdev;
     p.W = W;
     p.ldw = ldw;
     dim3 grid((chi_l + TL - 1) / TL, (chi_r + TR - 1) / TR);
@@ -371,8 +376,8 @@ template cudaError_t gemm_auto<c128>(const GemmDesc<c128>&, bool, int*, unsigned
 template cudaError_t gemm_simt<c64>(const GemmDesc<c64>&, cudaStream_t);
 template cudaError_t gemm_simt<c128>(const GemmDesc<c128>&, cudaStream_t);
 template cudaError_t theta_gemm_simt<c64>(int, int, int, const c64*, const c64*, const c64*, c64*,
-                                          int64_t, cudaStream_t);
+                                          int64_t, cudaStream_t, const c64*);
 template cudaError_t theta_gemm_simt<c128>(int, int, int, const c128*, const c128*, const c128*,
-                                           c128*, int64_t, cudaStream_t);
+                                           c128*, int64_t, cudaStream_t, const c128*);
 
 }  // namespace mpsg

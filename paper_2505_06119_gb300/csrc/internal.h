@@ -85,7 +85,7 @@ int choose_splitk(int M, int N, int K, int64_t cap_elems, int elem_bytes);
 // with the gate epilogue
 cudaError_t gemm_c64(const GemmDesc<c64>& d, cudaStream_t s);
 cudaError_t theta_c64(int cl, int cm, int cr, const c64* A, const c64* B, const c64* g16, c64* W, int64_t ldw,
-                      cudaStream_t s);
+                      cudaStream_t s, const c64* gdev = nullptr);
 int gemm_c64_tile_rows(int M, int K);
 
 // Tensor-core (tcgen05, 3xTF32) complex64 GEMM with the same operand views
@@ -93,7 +93,7 @@ int gemm_c64_tile_rows(int M, int K);
 bool tc_gemm_applicable(const GemmDesc<c64>& d);
 cudaError_t tc_gemm(const GemmDesc<c64>& d, int* err, unsigned long long timeout_ns, cudaStream_t s);
 cudaError_t tc_theta(int cl, int cm, int cr, const c64* A, const c64* B, const c64* g16, c64* W, int64_t ldw,
-                     int* err, unsigned long long timeout_ns, cudaStream_t s);
+                     int* err, unsigned long long timeout_ns, cudaStream_t s, const c64* gdev = nullptr);
 
 // GEMM dispatch: complex64 products go to the tensor cores when `use_tc` and
 // the shape suits them, everything else to gemm_simt.
@@ -103,10 +103,11 @@ cudaError_t gemm_auto(const GemmDesc<T>& d, bool use_tc, int* err, unsigned long
 // theta contraction with the gate epilogue (Sec. III-B.1 + III-C.2):
 //   X[(l,c),(d,r)] = sum_mu A[l,c,mu] B[mu,d,r]
 //   W[(b*chi_r + r)*ldw + 2l + a] = sum_{cd} g[2a+b][2c+d] X[(l,c),(d,r)]
-// A, B row-major sites; W column-major (2 chi_l) x (2 chi_r).
+// A, B row-major sites; W column-major (2 chi_l) x (2 chi_r).  gdev != NULL: the gate
+// is read from device memory there instead of g16 (layers replayed as CUDA graphs).
 template <typename T>
 cudaError_t theta_gemm_simt(int chi_l, int chi_m, int chi_r, const T* A, const T* B, const T* g16,
-                            T* W, int64_t ldw, cudaStream_t s);
+                            T* W, int64_t ldw, cudaStream_t s, const T* gdev = nullptr);
 
 // ---------------------------------------------------------------------------
 // Elementwise / data movement kernels
@@ -215,6 +216,7 @@ struct SmallGate {
   int* jpvt_out;       // optional: the pivot order (2 cr entries)
   int cl, cm, cr, k;
   T g[16];             // gate, g[(2a+b)*4 + (2c+d)]
+  const T* gdev;       // the gate in device memory instead (graph replay); NULL: g
 };
 
 template <typename T>

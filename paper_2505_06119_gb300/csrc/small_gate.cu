@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(SNT) small_gate_kernel(const __grid_constant__
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cl = G.cl, cm = G.cm, cr = G.cr, k = G.k;
   const int m = 2 * cl, n = 2 * cr;
-  if (tid < 16) s_g[tid] = G.g[tid];
+  if (tid < 16) s_g[tid] = G.gdev ? G.gdev[tid] : G.g[tid];
   // 1. X = A B (m x n), then theta with the gate epilogue
   for (int e = tid; e < m * n; e += SNT) {
     const int i = e % m, j = e / m;

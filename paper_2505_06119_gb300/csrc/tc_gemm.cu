@@ -65,6 +65,7 @@ struct TcArgs {
   int64_t ldc;
   int theta;  // 1: theta epilogue into W
   c64 g[16];
+  const c64* gdev;  // the gate in device memory instead (graph replay); NULL: g
   int cl, cr;
   c64* W;
   int64_t ldw;
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         if (store && l < a.cl && r < a.cr) {
 #pragma unroll
           for (int bb = 0; bb < 2; ++bb) {
-            const c64* gr = a.g + (2 * ca + bb) * 4;
+            const c64* gr = (a.gdev ? a.gdev : a.g) + (2 * ca + bb) * 4;
             c64 v = gr[0] * xc0d0;
             cfma(v, gr[1], xc0d1);
             cfma(v, gr[2], xc1d0);
@@ -451,7 +452,7 @@ cudaError_t tc_gemm(const GemmDesc<c64>& d, int* err, unsigned long long timeout
 }
 
 cudaError_t tc_theta(int cl, int cm, int cr, const c64* A, const c64* B, const c64* g16, c64* W, int64_t ldw,
-                     int* err, unsigned long long timeout_ns, cudaStream_t s) {
+                     int* err, unsigned long long timeout_ns, cudaStream_t s, const c64* gdev) {
   cudaError_t e = tc_setup();
   if (e != cudaSuccess) return e;
   TcArgs a;
@@ -479,6 +480,7 @@ cudaError_t tc_theta(int cl, int cm, int cr, const c64* A, const c64* B, const c
   a.K = cm;
   a.theta = 1;
   for (int i = 0; i < 16; ++i) a.g[i] = g16[i];
+  a.gdev = gdev;
   a.cl = cl;
   a.cr = cr;
   a.W = W;
