@@ -16,7 +16,9 @@
 //        (beta, 0, ..., 0) under H_j^H:  alpha = x_0,
 //        beta = -sign(Re alpha) * ||x|| (sign(0) = +1),
 //        tau = (beta - alpha) / beta,  v = (1, x_1.. / (alpha - beta));
-//        when ||x_1..|| = 0 and Im alpha = 0, tau = 0 and H_j = I;
+//        when ||x_1..|| = 0 and Im alpha = 0, tau = 0 and H_j = I; also when
+//        ||x||^2 is below the smallest normal double (the formula is undefined
+//        there: the squares underflow and alpha - beta rounds to zero);
 //     5. apply H_j^H = I - conj(tau) v v^H to A[j:m, j+1:n].
 //   After k steps the first k rows of A hold R (upper trapezoidal), the
 //   columns below the diagonal hold v (unit leading entry implicit) and the
@@ -39,6 +41,7 @@
 // threads; every element is computed by one thread in a fixed order, so the
 // result does not depend on the thread count.
 
+#include <cfloat>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -122,7 +125,7 @@ int cpqr_impl(int m, int n, int kmax, int pivot, cd* A, int64_t lda, cd* tau, in
     double xnorm2 = 0.0;
     for (int r = j + 1; r < m; ++r) xnorm2 += abs2(x[r]);
     cd tj = {0.0, 0.0};
-    if (xnorm2 == 0.0 && alpha.im == 0.0) {
+    if ((xnorm2 == 0.0 && alpha.im == 0.0) || abs2(alpha) + xnorm2 < DBL_MIN) {
       tj = {0.0, 0.0};  // H_j = I, column left as it is
     } else {
       double nrm = std::sqrt(alpha.re * alpha.re + alpha.im * alpha.im + xnorm2);

@@ -206,3 +206,19 @@ def test_replay_flags_a_non_greedy_step():
     assert c2[0] < m2[0]
     with pytest.raises(ValueError):
         qr.cpqr_replay(a, np.zeros(16, dtype=int))  # column 0 twice
+
+
+def test_column_of_underflowing_residue_gets_the_identity_reflector():
+    """A column whose entries' squares underflow (rounding residue around 1e-170 next to
+    O(1) columns): the reflector formula would divide by zero; the column is treated as
+    zero (tau = 0, R_jj = alpha) and the factorisation stays finite and exact."""
+    rng = np.random.default_rng(5)
+    a = cgauss(rng, 6, 4)
+    a[:, 1] = 0
+    a[:, 3] = 1e-170 * (1 + 1j) * cgauss(rng, 6, 1)[:, 0]
+    q, r, p, disc = qr.cpqr(a)
+    assert np.all(np.isfinite(q)) and np.all(np.isfinite(r))
+    assert np.abs(q.conj().T @ q - np.eye(4)).max() < 1e-12
+    assert np.abs(q @ r - a[:, p]).max() < 1e-14
+    f = qr.factor(a)
+    assert f["tau"][3] == 0
