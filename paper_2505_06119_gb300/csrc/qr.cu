@@ -88,13 +88,14 @@ struct PanelArgs {
   int* piv_seq;  // optional: the pivot position p taken at each step
 };
 
-// Squared column norm below which a reflector is the identity (tau = 0): in
-// complex64, 1/(alpha - beta) of such a column would not fit the data type (its
-// entries are below FLT_MIN, rounding residue of exact zeros), and rounding it to
-// FP32 would give inf and then NaN in v.  Complex128 keeps every nonzero column.
+// Squared column norm below which a reflector is the identity (tau = 0): the
+// smallest normal number of the data type's real part squared (complex64: FLT_MIN^2,
+// complex128: DBL_MIN).  Such a column holds rounding residue of exact zeros; its
+// entries' squares underflow, so ||x|| and alpha - beta would round to zero and
+// 1/(alpha - beta) to infinity, and v would turn into NaN.
 template <typename T>
 __device__ __forceinline__ double zero_column_level() {
-  return sizeof(T) == 8 ? 1.3814317e-76 : 0.0;  // FLT_MIN^2
+  return sizeof(T) == 8 ? 1.3814317e-76 : 2.2250738585072014e-308;
 }
 
 // Pivot key of a squared norm: for a non-negative double (or +inf) its bit
@@ -1768,15 +1769,17 @@ __global__ void sketch_solve_kernel(const T* Ys, int64_t ldy, int lsk, int j0, i
 }
 
 // Pivots of one block from the sketch: kb steps of column-pivoted Householder QR
-// on the l x nc matrix Yw (column-major, ld ldy), writing at step j the position
-// p that was swapped with j (the contract of PanelArgs::piv_seq) -- the same
-// pivots as the panel kernel (exact FP64 norms every step instead of downdated
-// ones; exact ties of squared norms go to the lowest original column).
+// on the l x nc matrix Y (column-major, ld ldy), writing at step j the position p
+// that was swapped with j (the contract of PanelArgs::piv_seq).  As in the panel
+// kernel, the squared column norms are FP64, downdated after every step
+// (vn1 -= |y_j|^2) and recomputed exactly when vn1 <= flag_tol * vn2 (vn2 = the last
+// exact value); exact ties of squared norms go to the lowest original column.
 // Cooperative grid, one grid barrier per step: every CTA keeps its share of the
-// columns in shared memory, publishes its best candidate (norm, column, and the
-// column's entries) in a double-buffered global slot, and after the barrier all
-// CTAs pick the same winner and build the same reflector in FP64, apply it to
-// their columns and recompute their norms.  CTA 0 keeps the position map.
+// columns in shared memory, row-major so that one thread per column reads and
+// updates it without bank conflicts, publishes its best candidate (norm, column and
+// the column's entries) in a double-buffered global slot, and after the barrier all
+// CTAs pick the same winner and build the same reflector in FP64.  CTA 0 keeps the
+// position map.
 constexpr int SKT = 256;  // threads of the sketch-pivot kernel
 constexpr int SKW = SKT / 32;
 
@@ -1793,7 +1796,18 @@ struct SketchPivArgs {
   int* err;
   unsigned expected;
   unsigned long long timeout_ns;
+  double flag_tol;
 };
+
+template <typename T>
+__device__ __forceinline__ double sk_col_norm2(const T* ys, int nl, int c, int r0, int l) {
+  double s2 = 0.0;
+  for (int r = r0; r < l; ++r) {
+    const T x = ys[r * nl + c];
+    s2 += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
+  }
+  return s2;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) {
@@ -1804,18 +1818,19 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
   int c0, c1;
   split_range(0, a.nc, G, b, c0, c1);
   const int nl = c1 - c0;
-  T* ys = reinterpret_cast<T*>(sk_smem);                          // l x nl, ld l
-  double* nrm = reinterpret_cast<double*>(ys + (int64_t)l * nl);  // nl squared norms (< 0: consumed)
-  T* xw = reinterpret_cast<T*>(nrm + ((nl + 1) & ~1));             // the winner's column, l entries (16-byte aligned)
+  T* ys = reinterpret_cast<T*>(sk_smem);                          // l x nl, row-major (row r at ys + r nl)
+  double* vn1 = reinterpret_cast<double*>(ys + (int64_t)l * nl);  // nl squared norms (< 0: consumed)
+  double* vn2 = vn1 + nl;                                         // nl: the last exact values
+  T* xw = reinterpret_cast<T*>(vn2 + ((nl + 1) & ~1));             // the winner's column, l entries
   __shared__ double s_bv[SKW];
   __shared__ int s_bi[SKW];
-  __shared__ int s_win;
+  __shared__ int s_win, s_wb;
   __shared__ c128 s_tau, s_sc;
   __shared__ int s_skip;
   if (tid == 0) s_skip = ld_relaxed_i32(a.err) != DEV_OK;
   for (int e = tid; e < l * nl; e += SKT) {
-    const int r = e % l, c = e / l;
-    ys[e] = a.Y[r + (int64_t)(c0 + c) * a.ldy];
+    const int c = e / l, r = e - c * l;  // coalesced reads along each column
+    ys[r * nl + c] = a.Y[r + (int64_t)(c0 + c) * a.ldy];
   }
   if (b == 0)
     for (int c = tid; c < a.nc; c += SKT) {
@@ -1824,26 +1839,20 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
     }
   __syncthreads();
   if (s_skip) return;
+  for (int c = tid; c < nl; c += SKT) {
+    const double s2 = sk_col_norm2(ys, nl, c, 0, l);
+    vn1[c] = s2;
+    vn2[c] = s2;
+  }
+  __syncthreads();
   const int slot = l + 2;  // published entries per CTA: norm, column index, the column
   for (int j = 0; j < a.kb; ++j) {
-    // exact squared norms of rows j..l-1 of the local columns, one warp per column
-    for (int c = warp; c < nl; c += SKW) {
-      if (j > 0 && nrm[c] < 0.0) continue;  // consumed (lane-uniform)
-      double s2 = 0.0;
-      for (int r = j + lane; r < l; r += 32) {
-        const T x = ys[r + c * l];
-        s2 += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
-      }
-      s2 = warp_sum(s2);
-      if (lane == 0) nrm[c] = s2;
-    }
-    __syncthreads();
     // local candidate: the largest norm, the lowest column on ties
     double bv = -1.0;
     int bi = 0x7fffffff;
     for (int c = tid; c < nl; c += SKT)
-      if (nrm[c] > bv) {  // ascending c per thread
-        bv = nrm[c];
+      if (vn1[c] > bv) {  // ascending c per thread
+        bv = vn1[c];
         bi = c0 + c;
       }
     for (int o = 16; o > 0; o >>= 1) {
@@ -1873,7 +1882,7 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
     __syncthreads();
     if (s_bi[0] >= c0 && s_bi[0] < c1) {
       const int c = s_bi[0] - c0;
-      for (int r = tid; r < l; r += SKT) pub[2 + r] = ys[r + c * l];
+      for (int r = tid; r < l; r += SKT) pub[2 + r] = ys[r * nl + c];
     }
     if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
     // the winner over all CTAs (identical in every CTA)
@@ -1902,11 +1911,11 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
       }
       if (lane == 0) {
         s_win = wi;
-        s_bi[1] = wb;
+        s_wb = wb;
       }
     }
     __syncthreads();
-    const int win = s_win, wb = s_bi[1];
+    const int win = s_win, wb = s_wb;
     if (win < 0 || win >= a.nc) {  // only reachable with non-finite norms
       if (tid == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_NONFINITE);
       return;
@@ -1951,22 +1960,29 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
     __syncthreads();
     const T sc = ccast<R>(s_sc), ctau = cconj(ccast<R>(s_tau));
     for (int r = j + 1 + tid; r < l; r += SKT) xw[r] = xw[r] * sc;  // v (v_j = 1 implicit)
-    if (win >= c0 && win < c1 && tid == 0) nrm[win - c0] = -1.0;    // consumed
+    if (win >= c0 && win < c1 && tid == 0) vn1[win - c0] = -1.0;    // consumed
     __syncthreads();
-    if (!(s_tau.re == 0.0 && s_tau.im == 0.0)) {
-      for (int c = warp; c < nl; c += SKW) {
-        if (nrm[c] < 0.0) continue;
-        T* y = ys + c * l;
-        const T top = y[j];
-        T d = mk<R>(0, 0);
-        for (int r = j + 1 + lane; r < l; r += 32) cfma_conj(d, xw[r], y[r]);
-        d.re = warp_sum(d.re);
-        d.im = warp_sum(d.im);
-        d = d + top;
+    const bool apply = !(s_tau.re == 0.0 && s_tau.im == 0.0);
+    // one thread per remaining column: H^H applied, then the FP64 norm downdate
+    for (int c = tid; c < nl; c += SKT) {
+      if (vn1[c] < 0.0) continue;
+      T yj = ys[j * nl + c];
+      if (apply) {
+        T d = yj;
+        for (int r = j + 1; r < l; ++r) cfma_conj(d, xw[r], ys[r * nl + c]);
         const T f = ctau * d;
-        __syncwarp();
-        if (lane == 0) y[j] = top - f;
-        for (int r = j + 1 + lane; r < l; r += 32) y[r] = y[r] - xw[r] * f;
+        yj = yj - f;
+        ys[j * nl + c] = yj;
+        for (int r = j + 1; r < l; ++r) ys[r * nl + c] = ys[r * nl + c] - xw[r] * f;
+      }
+      const double r2 = (double)yj.re * (double)yj.re + (double)yj.im * (double)yj.im;
+      const double v1 = fmax(vn1[c] - r2, 0.0);
+      if (v1 <= a.flag_tol * vn2[c]) {
+        const double e2 = sk_col_norm2(ys, nl, c, j + 1, l);
+        vn1[c] = e2;
+        vn2[c] = e2;
+      } else {
+        vn1[c] = v1;
       }
     }
     __syncthreads();
@@ -1975,7 +1991,7 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
 
 template <typename T>
 static size_t sketch_piv_smem(int l, int nl) {
-  return (size_t)l * nl * sizeof(T) + (size_t)((nl + 1) & ~1) * 8 + (size_t)l * sizeof(T);
+  return (size_t)l * nl * sizeof(T) + (size_t)nl * 8 + (size_t)((nl + 1) & ~1) * 8 + (size_t)l * sizeof(T);
 }
 
 // Launch sketch_pivots_kernel for the l x nc sketch Y (pub: 2 G (l + 2) elements of
@@ -1983,7 +1999,7 @@ static size_t sketch_piv_smem(int l, int nl) {
 template <typename T>
 static cudaError_t launch_sketch_pivots(const T* Y, int64_t ldy, int l, int nc, int kb, int* piv_seq, int* maps,
                                         T* pub, int64_t pub_cap, unsigned* bar, int* err, unsigned barrier_extra,
-                                        unsigned long long timeout_ns, cudaStream_t s) {
+                                        unsigned long long timeout_ns, double flag_tol, cudaStream_t s) {
   static PerDevice once;
   cudaError_t attr = cudaSuccess;
   once.get([&attr]() -> long long {
@@ -1991,10 +2007,10 @@ static cudaError_t launch_sketch_pivots(const T* Y, int64_t ldy, int l, int nc, 
     return attr == cudaSuccess ? 1 : -1;
   });
   if (attr != cudaSuccess) return attr;
-  // about 512 columns per CTA: the per-step work is a few microseconds of shared-memory
-  // arithmetic, so few CTAs keep the grid barrier and the winner scan short; more CTAs
-  // only where the columns do not fit one CTA's shared memory (one CTA per SM at most)
-  int G = std::max(1, std::min(num_sms(), (nc + 511) / 512));
+  // about 128 columns per CTA (one thread per column does a step's work in a few
+  // hundred cycles, so the grid barrier sets the pace); more CTAs where the columns
+  // do not fit one CTA's shared memory (one CTA per SM at most)
+  int G = std::max(1, std::min(num_sms(), (nc + 127) / 128));
   while (G < num_sms() && sketch_piv_smem<T>(l, (nc + G - 1) / G) > (size_t)(160 * 1024)) ++G;
   const size_t smem = sketch_piv_smem<T>(l, (nc + G - 1) / G);
   if (smem > (size_t)kPanelSmem || 2 * (int64_t)G * (l + 2) > pub_cap) return cudaErrorInvalidConfiguration;
@@ -2012,6 +2028,7 @@ static cudaError_t launch_sketch_pivots(const T* Y, int64_t ldy, int l, int nc, 
   a.err = err;
   a.expected = (unsigned)G + barrier_extra;
   a.timeout_ns = timeout_ns;
+  a.flag_tol = flag_tol;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)sketch_pivots_kernel<T>, dim3(G), dim3(SKT), args, smem, s);
 }
@@ -2066,7 +2083,7 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
     //    then the same column swaps on W, on the sketch and on jpvt
     hook_before(hooks, K(MPS_KCLASS_PANEL), (double)l * nr * sizeof(T), 8.0 * l * nr * kb);
     CK(launch_sketch_pivots<T>(p.Ys + (int64_t)j0 * ldy, ldy, l, nr, kb, p.piv_seq, reinterpret_cast<int*>(p.vn1),
-                               p.SK, p.sk_cap, p.bar, p.err, p.barrier_extra, p.timeout_ns, s));
+                               p.SK, p.sk_cap, p.bar, p.err, p.barrier_extra, p.timeout_ns, p.flag_tol, s));
     apply_swaps_kernel<T><<<std::max(1, std::min(1024, (m + 255) / 256)), 256, 0, s>>>(p.W, p.ldw, m, j0, p.piv_seq,
                                                                                       kb, p.jpvt);
     CK(cudaGetLastError());

@@ -10,8 +10,9 @@
 //      squared norms of the remaining columns every step, the largest taken (the
 //      lowest index on ties), beta = -sign(Re alpha) ||x||, tau = (beta - alpha) /
 //      beta, v = (1, x_1.. / (alpha - beta)) with FP64 scalars, H^H applied to the
-//      columns to the right; the identity reflector for a column without a tail,
-//      and in complex64 for one whose norm is below FLT_MIN (as the grid kernels);
+//      columns to the right; the identity reflector for a column without a tail
+//      or one whose squared norm is below the smallest normal number (as the grid
+//      kernels);
 //   3. the discarded weight ||theta[k:, k:]||_F^2 in FP64;
 //   4. Q[:, :k] = H_0 ... H_{k-1} I, then the left site Q and the right site R P^T.
 //
@@ -28,9 +29,11 @@ constexpr int SNT = 256;        // threads per CTA
 constexpr int SNW = SNT / 32;
 constexpr int LD = kSmallDim;   // leading dimension of theta and Q in shared memory
 
+// squared column norm below which the reflector is the identity: FLT_MIN^2 for
+// complex64, DBL_MIN for complex128 (rounding residue whose squares underflow)
 template <typename T>
 __device__ __forceinline__ double small_zero_level() {
-  return sizeof(T) == 8 ? 1.3814317e-76 : 0.0;  // FLT_MIN^2 for complex64
+  return sizeof(T) == 8 ? 1.3814317e-76 : 2.2250738585072014e-308;
 }
 
 template <typename T>
