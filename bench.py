@@ -606,19 +606,30 @@ def layer_workload(args):
     from paper_2505_06119_gb300 import MPS
 
     n = 64
+    modes = args.layer_modes.split(",")
     out = {"workload": "layer", "n_sites": n, "precision": "mixed", "policy": "local", "rows": []}
     for chi in [int(c) for c in args.layer_chi.split(",")]:
-        sites = [s.astype(np.complex64) for s in states.random_canonical_mps(n, states.max_bond_dims(n, chi), n // 2,
-                                                                            seed=5)]
+        bonds_ = states.max_bond_dims(n, chi)
+        if chi >= 4096:
+            # saturated i.i.d. Gaussian sites (the local policy needs no canonical form, and
+            # a layer's work depends only on the bond dims); generated in complex64
+            rng0 = np.random.default_rng(5)
+            sites = []
+            for i in range(n):
+                shp = (bonds_[i], 2, bonds_[i + 1])
+                x = rng0.standard_normal(shp, dtype=np.float32) + 1j * rng0.standard_normal(shp, dtype=np.float32)
+                sites.append((x / np.float32(np.sqrt(2.0 * bonds_[i]))).astype(np.complex64))
+        else:
+            sites = [s.astype(np.complex64) for s in states.random_canonical_mps(n, bonds_, n // 2, seed=5)]
         rng = np.random.default_rng(3)
         row = {"chi": chi}
         for par in (0, 1):
             bonds = list(range(par, n - 1, 2))
             gs = [gates.haar_unitary(rng, 4) for _ in bonds]
-            res = {}
-            for mode in ("layer", "layer_direct", "one_by_one"):
+            res = {"layer_direct": None, "one_by_one": None, "graph_launches": None}
+            for mode in [x for x in ("layer", "layer_direct", "one_by_one") if x in modes]:
                 with MPS(n, chi, precision="mixed", policy="local", graphs=(mode == "layer")) as m:
-                    for rep in range(3):  # two warm-up layers (the second one captures the graph), then timed
+                    for rep in range(3 if chi < 4096 else 2):  # warm-up layers (the second captures the graph)
                         m.set_sites(sites, centre=n // 2)
                         m.sync()
                         torch.cuda.synchronize()
@@ -632,11 +643,12 @@ def layer_workload(args):
                         res[mode] = (time.perf_counter() - t) * 1e3
                     if mode == "layer":
                         res["graph_launches"] = m.layer_stats()[1]
-            row["even" if par == 0 else "odd"] = {"gates": len(bonds), "ms_layer": res["layer"],
-                                                  "ms_layer_direct": res["layer_direct"],
-                                                  "ms_one_by_one": res["one_by_one"],
-                                                  "graph_launches": res["graph_launches"],
-                                                  "speedup": res["one_by_one"] / res["layer"]}
+            row["even" if par == 0 else "odd"] = {
+                "gates": len(bonds), "ms_layer": res.get("layer"), "ms_layer_direct": res["layer_direct"],
+                "ms_one_by_one": res["one_by_one"], "graph_launches": res["graph_launches"],
+                "speedup": res["one_by_one"] / res["layer"] if res["one_by_one"] and res.get("layer") else None}
+            if args.layer_even_only:
+                break
         out["rows"].append(row)
     print(json.dumps(out), flush=True)
 
@@ -669,14 +681,15 @@ def circuit_workload(args):
         rows, cols, cyc = (int(x) for x in args.grid.split("x"))
         n, chi = rows * cols, args.grid_chi
         if args.circuit == "grid":
-            ops = circuits.grid_rcs(rows, cols, cyc, seed=11)
+            ops = circuits.grid_rcs(rows, cols, cyc, seed=11, singles=args.singles)
             how = "SWAP-routed vertical couplers (chains there and back)"
         else:
-            ops = circuits.grid_rcs_permuted(rows, cols, cyc, seed=11)
+            ops = circuits.grid_rcs_permuted(rows, cols, cyc, seed=11, singles=args.singles)
             how = ("vertical couplers in a column-snake embedding reached by bubble-sort site "
                    "permutations between the A/B and C/D layers")
-        name = ("%dx%d grid random circuit, %d cycles ABCDCDAB, paper 1q gate set and fSim, %s, chi_max=%d, "
-                "seed 11" % (rows, cols, cyc, how, chi))
+        ones = "paper 1q gate set" if args.singles == "paper" else "Haar 1q gates"
+        name = ("%dx%d grid random circuit, %d cycles ABCDCDAB, %s and fSim, %s, chi_max=%d, "
+                "seed 11" % (rows, cols, cyc, ones, how, chi))
     n2q = circuits.count_two_qubit(ops)
     swaps = sum(2 * (abs(op[2] - op[1]) - 1) for op in ops if op[0] == "2q") + \
         sum(circuits.inversions(op[1]) for op in ops if op[0] == "perm")
@@ -717,11 +730,22 @@ def circuit_workload(args):
     o = mm.overlap(m64)
     dev_o = 1.0 - abs(o) ** 2 / (mm.overlap(mm).real * m64.overlap(m64).real)
     dev_f = abs(res["mixed"]["fidelity"] - res["fp64"]["fidelity"]) / res["fp64"]["fidelity"]
+    rng = np.random.default_rng(2024)
+    amax = dmax = 0.0
+    for _ in range(64):  # sampled amplitudes, mixed against FP64
+        bits = rng.integers(0, 2, n)
+        a64 = m64.amplitude(bits)
+        dmax = max(dmax, abs(mm.amplitude(bits) - a64))
+        amax = max(amax, abs(a64))
+    dsc_mx, dsc_64 = mm.discarded()[0], m64.discarded()[0]
     for m in states_.values():
         m.close()
     print(json.dumps({"workload": "circuit", "circuit": name, "two_qubit_gates": n2q, "swaps": swaps, "paths": res,
                       "speedup_mixed_vs_fp64": res["fp64"]["seconds"] / res["mixed"]["seconds"],
-                      "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o}}), flush=True)
+                      "fidelity_dev": {"norm_fidelity_rel": dev_f, "overlap": dev_o, "amplitude_max_abs": dmax,
+                                       "amplitude_max_rel": dmax / amax if amax else None,
+                                       "discarded_total_rel": abs(dsc_mx - dsc_64) / max(dsc_64, 1e-300)}}),
+          flush=True)
 
 
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # CUDA-core FFMA peak at the 2070 MHz maximum clock
@@ -965,9 +989,13 @@ def main():
     ap.add_argument("--svd-gate-chi", default="64,256,512")
     ap.add_argument("--big-chi", type=int, default=16384)
     ap.add_argument("--layer-chi", default="256,1024,2048")
+    ap.add_argument("--layer-modes", default="layer,layer_direct,one_by_one")
+    ap.add_argument("--layer-even-only", action="store_true")
     ap.add_argument("--circuit", default="config2", choices=["config2", "grid", "grid-perm"])
     ap.add_argument("--grid-chi", type=int, default=256)
     ap.add_argument("--grid", default="7x7x12", help="rows x cols x cycles of the grid circuit")
+    ap.add_argument("--singles", default="paper", choices=["paper", "haar"],
+                    help="one-qubit gates of the grid circuit: the paper's sqrt X/Y/W set or Haar SU(2)")
     args = ap.parse_args()
     if args.workload == "layer":
         layer_workload(args)

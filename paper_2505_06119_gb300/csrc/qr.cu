@@ -1818,10 +1818,14 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
   int c0, c1;
   split_range(0, a.nc, G, b, c0, c1);
   const int nl = c1 - c0;
+  // carve-up of the dynamic shared memory, every part starting on a 16-byte boundary
+  // (l * nl * sizeof(T) is a multiple of 16 for the even sketch heights used; each
+  // norm array is rounded up to an even count of doubles)
+  const int nl2 = (nl + 1) & ~1;
   T* ys = reinterpret_cast<T*>(sk_smem);                          // l x nl, row-major (row r at ys + r nl)
   double* vn1 = reinterpret_cast<double*>(ys + (int64_t)l * nl);  // nl squared norms (< 0: consumed)
-  double* vn2 = vn1 + nl;                                         // nl: the last exact values
-  T* xw = reinterpret_cast<T*>(vn2 + ((nl + 1) & ~1));             // the winner's column, l entries
+  double* vn2 = vn1 + nl2;                                        // nl: the last exact values
+  T* xw = reinterpret_cast<T*>(vn2 + nl2);                        // the winner's column, l entries
   __shared__ double s_bv[SKW];
   __shared__ int s_bi[SKW];
   __shared__ int s_win, s_wb;
@@ -1991,7 +1995,7 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
 
 template <typename T>
 static size_t sketch_piv_smem(int l, int nl) {
-  return (size_t)l * nl * sizeof(T) + (size_t)nl * 8 + (size_t)((nl + 1) & ~1) * 8 + (size_t)l * sizeof(T);
+  return (size_t)l * nl * sizeof(T) + 2 * (size_t)((nl + 1) & ~1) * 8 + (size_t)l * sizeof(T);
 }
 
 // Launch sketch_pivots_kernel for the l x nc sketch Y (pub: 2 G (l + 2) elements of
@@ -2014,6 +2018,7 @@ static cudaError_t launch_sketch_pivots(const T* Y, int64_t ldy, int l, int nc, 
   while (G < num_sms() && sketch_piv_smem<T>(l, (nc + G - 1) / G) > (size_t)(160 * 1024)) ++G;
   const size_t smem = sketch_piv_smem<T>(l, (nc + G - 1) / G);
   if (smem > (size_t)kPanelSmem || 2 * (int64_t)G * (l + 2) > pub_cap) return cudaErrorInvalidConfiguration;
+  if (sizeof(T) == 8 && (l & 1)) return cudaErrorInvalidValue;  // the norm arrays must start 16-byte aligned
   SketchPivArgs<T> a;
   a.Y = Y;
   a.ldy = ldy;
