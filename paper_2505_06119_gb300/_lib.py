@@ -116,20 +116,33 @@ SIGNATURES = {
     "mps_last_split_pivots": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 
+CHECKED_LIB_PATH = os.path.join(HERE, "_build_checked", "libmps_gb300_checked.so")
+
 _lib = None
+_checked = None
 
 
-def load(path=LIB_PATH):
-    global _lib
-    if _lib is not None:
-        return _lib
+def _open(path):
     if not os.path.exists(path):
-        raise ImportError("libmps_gb300.so not built (%s); run paper_2505_06119_gb300/build.py "
-                          "or __graft_entry__.build()" % path)
+        raise ImportError("%s not built; run paper_2505_06119_gb300/build.py or __graft_entry__.build()" % path)
     lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
+
+
+def load(path=LIB_PATH):
+    global _lib
+    if _lib is None:
+        _lib = _open(path)
+    return _lib
+
+
+def load_checked():
+    """The bounds-checking build of the library (compiled with -DMPS_BOUNDS_CHECK)."""
+    global _checked
+    if _checked is None:
+        _checked = _open(CHECKED_LIB_PATH)
+    return _checked

@@ -16,6 +16,10 @@ ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmps_gb300.so")
+# the bounds-checking variant (-DMPS_BOUNDS_CHECK): kernels verify indices taken from
+# device data and report DEV_ERR_BOUNDS instead of accessing out of range
+CHECKED_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libmps_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,12 +49,16 @@ def _compile(src, obj, extra):
     return r.stderr
 
 
-def build(force=False, verbose=False, extra=()):
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, extra=(), checked=False):
+    """Build the library (checked=True: the bounds-checking variant) and return its path."""
+    out_dir = CHECKED_DIR if checked else OUT_DIR
+    lib = CHECKED_LIB if checked else LIB
+    extra = list(extra) + (["-DMPS_BOUNDS_CHECK"] if checked else [])
+    os.makedirs(out_dir, exist_ok=True)
     hdr_time = max(os.path.getmtime(h) for h in headers())
     objs, todo = [], []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_time):
             todo.append((src, obj))
@@ -61,17 +69,17 @@ def build(force=False, verbose=False, extra=()):
                 msg = f.result()
                 if verbose and msg:
                     print(futs[f], msg, file=sys.stderr)
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if todo or not os.path.exists(lib):
+        tmp = lib + ".tmp.%d" % os.getpid()
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     force = "--force" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(force=force, verbose=True, extra=extra))
+    print(build(force=force, verbose=True, extra=extra, checked="--checked" in sys.argv))

@@ -85,6 +85,19 @@ enum : int {
   DEV_ERR_NONFINITE = 3  // a NaN/Inf reached a pivot decision
 };
 
+// Index checks of the bounds-checking build (compiled with -DMPS_BOUNDS_CHECK): where
+// an index comes from device data (a permutation, a pivot sequence), a value outside
+// its range records DEV_ERR_BOUNDS in the device error word (when one is given) and
+// the access is skipped.  The ordinary build compiles the check to `true`.
+#ifdef MPS_BOUNDS_CHECK
+__device__ __forceinline__ bool index_ok(bool in_range, int* err) {
+  if (!in_range && err) atomicCAS(err, 0, 2);  // DEV_OK -> DEV_ERR_BOUNDS
+  return in_range;
+}
+#else
+__device__ __forceinline__ bool index_ok(bool, int*) { return true; }
+#endif
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -50,14 +50,17 @@ __global__ void copy2d_kernel(const T* src, int64_t lds, T* dst, int64_t ldd, in
   dst[r * ldd + c] = conj ? cconj(v) : v;
 }
 
-__global__ void invert_perm_kernel(const int* jpvt, int* inv, int n) {
+__global__ void invert_perm_kernel(const int* jpvt, int* inv, int n, int* err) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) inv[jpvt[t]] = t;
+  if (t < n) {
+    const int q = jpvt[t];
+    if (index_ok(q >= 0 && q < n, err)) inv[q] = t;
+  }
 }
 
 // site[kk*n + c] = R(kk, inv[c]),  R(kk, t) = kk <= t ? W[kk + t*ldw] : 0
 template <typename T>
-__global__ void split_right_kernel(const T* W, int64_t ldw, const int* inv, int k, int n, T* site) {
+__global__ void split_right_kernel(const T* W, int64_t ldw, const int* inv, int k, int n, T* site, int* err) {
   using R = typename real_of<T>::type;
   __shared__ T tile[32][33];  // [c][kk]
   const int k0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -67,7 +70,7 @@ __global__ void split_right_kernel(const T* W, int64_t ldw, const int* inv, int 
     T v = mk<R>(0, 0);
     if (c < n && kk < k) {
       int t = inv[c];
-      if (kk <= t) v = W[kk + (int64_t)t * ldw];
+      if (kk <= t && index_ok(t < n, err)) v = W[kk + (int64_t)t * ldw];
     }
     tile[i][tx] = v;
   }
@@ -172,14 +175,15 @@ cudaError_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int rows, int
 }
 
 template <typename T>
-cudaError_t split_right(const T* W, int64_t ldw, const int* jpvt, int* inv, int k, int n, T* site, cudaStream_t s) {
+cudaError_t split_right(const T* W, int64_t ldw, const int* jpvt, int* inv, int k, int n, T* site, cudaStream_t s,
+                        int* err) {
   if (k <= 0 || n <= 0) return cudaSuccess;
-  invert_perm_kernel<<<blocks_for(n, 256), 256, 0, s>>>(jpvt, inv, n);
+  invert_perm_kernel<<<blocks_for(n, 256), 256, 0, s>>>(jpvt, inv, n, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid((n + 31) / 32, (k + 31) / 32);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  split_right_kernel<T><<<grid, dim3(32, 8), 0, s>>>(W, ldw, inv, k, n, site);
+  split_right_kernel<T><<<grid, dim3(32, 8), 0, s>>>(W, ldw, inv, k, n, site, err);
   return cudaGetLastError();
 }
 
@@ -219,7 +223,7 @@ cudaError_t vecmat(const c128* v, const T* M, int64_t ld, int rows, int cols, c1
   template cudaError_t apply_1q<T>(T*, int, int, const T*, cudaStream_t);                            \
   template cudaError_t transpose_copy<T>(const T*, int64_t, T*, int64_t, int, int, int, cudaStream_t); \
   template cudaError_t copy2d<T>(const T*, int64_t, T*, int64_t, int, int, int, cudaStream_t);        \
-  template cudaError_t split_right<T>(const T*, int64_t, const int*, int*, int, int, T*, cudaStream_t); \
+  template cudaError_t split_right<T>(const T*, int64_t, const int*, int*, int, int, T*, cudaStream_t, int*); \
   template cudaError_t set_identity<T>(T*, int64_t, int, int, cudaStream_t);                         \
   template cudaError_t norm2_sum<T>(const T*, int64_t, double*, int, double*, cudaStream_t);         \
   template cudaError_t vecmat<T>(const c128*, const T*, int64_t, int, int, c128*, cudaStream_t);

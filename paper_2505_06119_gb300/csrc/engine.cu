@@ -289,7 +289,7 @@ cudaError_t two_site_core(const Ws<T>& w, const Knobs& kn, int cl, int cm, int c
   // left site (row-major m x k) <- Q (column-major m x k)
   CKE(transpose_copy<T>(w.Q, w.ldq, Aout, k, k, m, 0, s));
   // right site (row-major k x n) <- R P^T
-  CKE(split_right<T>(w.W, w.ldw, w.jpvt, w.inv, k, n, Bout, s));
+  CKE(split_right<T>(w.W, w.ldw, w.jpvt, w.inv, k, n, Bout, s, w.err));
   hook_after(hk, MPS_KCLASS_SPLIT, 3);
   return cudaSuccess;
 }
@@ -1094,7 +1094,7 @@ int apply_mpo_t(mps_t h, int first, int count, const int* bonds, const mps_c128*
     if (e != cudaSuccess) return cuda_fail(h, e, "apply_mpo: split");
     hook_before(hk, MPS_KCLASS_SPLIT, 2.0 * ((double)m * k + (double)k * nn) * sizeof(T), 0);
     e = transpose_copy<T>(w.Q, w.ldq, (T*)h->site[i], k, k, m, 0, h->stream);
-    if (e == cudaSuccess) e = split_right<T>(w.W, w.ldw, w.jpvt, w.inv, k, nn, C, h->stream);
+    if (e == cudaSuccess) e = split_right<T>(w.W, w.ldw, w.jpvt, w.inv, k, nn, C, h->stream, w.err);
     hook_after(hk, MPS_KCLASS_SPLIT, 3);
     if (e != cudaSuccess) return cuda_fail(h, e, "apply_mpo: split");
     h->bond[i + 1] = k;

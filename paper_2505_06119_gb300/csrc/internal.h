@@ -124,9 +124,10 @@ cudaError_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int rows, int
 // Left split: site (row-major m x k, ld k) = Q (col-major m x k, ldq)
 // Right split: site[kk*n + c] = R[kk, pos(c)] with pos = inverse of jpvt
 // (R: first k rows of column-major W, upper trapezoidal; zero below).
+// err: the device error word for the bounds-checking build's checks of jpvt (may be NULL)
 template <typename T>
 cudaError_t split_right(const T* W, int64_t ldw, const int* jpvt, int* inv_scratch, int k, int n,
-                        T* site, cudaStream_t s);
+                        T* site, cudaStream_t s, int* err = nullptr);
 template <typename T>
 cudaError_t set_identity(T* Q, int64_t ldq, int m, int k, cudaStream_t s);
 template <typename TO, typename TI>

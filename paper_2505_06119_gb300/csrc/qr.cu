@@ -1710,9 +1710,14 @@ __global__ void sketch_omega_kernel(T* Om, int64_t ldy, int lsk, int m, unsigned
 // order, swap columns j0 + t and j0 + seq[t] of A (rows [0, rows)); with jpvt the
 // same swaps are made on jpvt (block 0).
 template <typename T>
-__global__ void apply_swaps_kernel(T* A, int64_t lda, int rows, int j0, const int* seq, int kb, int* jpvt) {
+__global__ void apply_swaps_kernel(T* A, int64_t lda, int rows, int j0, const int* seq, int kb, int* jpvt, int nc,
+                                   int* err) {
   __shared__ int s_seq[kPanelNbMax];
-  if (threadIdx.x < kb) s_seq[threadIdx.x] = seq[threadIdx.x];
+  if (threadIdx.x < kb) {
+    const int q = seq[threadIdx.x];
+    // a position outside [t, nc) would be an out-of-range column: the swap is skipped
+    s_seq[threadIdx.x] = index_ok(q >= (int)threadIdx.x && q < nc, err) ? q : (int)threadIdx.x;
+  }
   __syncthreads();
   if (jpvt && blockIdx.x == 0 && threadIdx.x == 0) {
     for (int t = 0; t < kb; ++t) {
@@ -2090,9 +2095,9 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
     CK(launch_sketch_pivots<T>(p.Ys + (int64_t)j0 * ldy, ldy, l, nr, kb, p.piv_seq, reinterpret_cast<int*>(p.vn1),
                                p.SK, p.sk_cap, p.bar, p.err, p.barrier_extra, p.timeout_ns, p.flag_tol, s));
     apply_swaps_kernel<T><<<std::max(1, std::min(1024, (m + 255) / 256)), 256, 0, s>>>(p.W, p.ldw, m, j0, p.piv_seq,
-                                                                                      kb, p.jpvt);
+                                                                                      kb, p.jpvt, nr, p.err);
     CK(cudaGetLastError());
-    apply_swaps_kernel<T><<<1, 256, 0, s>>>(p.Ys, ldy, l, j0, p.piv_seq, kb, nullptr);
+    apply_swaps_kernel<T><<<1, 256, 0, s>>>(p.Ys, ldy, l, j0, p.piv_seq, kb, nullptr, nr, p.err);
     CK(cudaGetLastError());
     hook_after(hooks, K(MPS_KCLASS_PANEL), 3);
     PanelArgs<T> a;

@@ -52,8 +52,8 @@ def config(precision="fp64", policy="canon", panel_width=0, stream=None, profile
 class MPS:
     """An n-qubit MPS on the GPU (handle of the C library)."""
 
-    def __init__(self, n, chi_max, precision="fp64", policy="canon", **kw):
-        self.lib = L.load()
+    def __init__(self, n, chi_max, precision="fp64", policy="canon", lib=None, **kw):
+        self.lib = lib if lib is not None else L.load()
         self.n = n
         self.chi_max = chi_max
         self.precision = precision
