@@ -52,7 +52,7 @@
  *     permutation of a split, the column swaps of randomized pivoting) check
  *     them in the library built with -DMPS_BOUNDS_CHECK, and a value out of
  *     range then records the failure (MPS_E_CUDA, "device-side check failed")
- *     instead of an access out of range; the ordinary build leaves them out. */
+ *     instead of an access out of range; the ordinary build leaves them out.
  *   - A handle is not thread-safe; distinct handles may be used from distinct
  *     threads, and on distinct devices.  What the library sets up at first use
  *     (kernel attributes, occupancy, cluster sizes) is kept per device. */
