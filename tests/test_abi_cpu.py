@@ -106,3 +106,19 @@ def test_workspace_query_is_host_only(lib):
     assert sz.value > small
     assert lib.mps_two_site_workspace(L.MPS_PREC_MIXED, 128, 128, 128, 128, ctypes.byref(sz)) == L.MPS_OK
     assert lib.mps_two_site_workspace(L.MPS_PREC_FP64, 0, 1, 1, 1, ctypes.byref(sz)) == L.MPS_E_ARG
+
+
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_header_compiles_as_c_and_cpp(lang, tmp_path):
+    """include/mps.h is a plain C header usable from C and C++ callers."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("use.c" if lang == "c" else "use.cpp")
+    src.write_text('#include "mps.h"\nint main(void) { mps_config c; mps_config_init(&c); return c.precision; }\n')
+    r = subprocess.run([cc, "-x", lang, "-fsyntax-only", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
