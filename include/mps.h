@@ -66,6 +66,12 @@
 extern "C" {
 #endif
 
+/* The library is built with hidden symbol visibility; the declarations of this header
+ * are its only exports. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 #define MPS_OK 0
 #define MPS_E_ARG (-1)         /* invalid argument (checked on the host, nothing launched) */
 #define MPS_E_NOMEM (-2)       /* a device or pinned-host allocation failed */
@@ -90,8 +96,9 @@ extern "C" {
 
 #define MPS_TRUNC_RQRCP 2 /* truncated QR with randomized column pivoting (blocked RQRCP of Duersch-Gu and
                             Martinsson et al.; one of the QR improvements Sec. IV-A.1 points to): the
-                            pivots of each block of panel-width columns come from a pivoted QR of a
-                            small random sketch Y = Omega theta (panel width + 8 rows, entries +-1
+                            pivots of each block of twice the panel width (64 columns by default)
+                            come from a pivoted QR of a small random sketch Y = Omega theta (block
+                            width + 8 rows, entries +-1
                             from SplitMix64 with state sketch_seed + s for the s-th two-site split of
                             the handle), the block itself is factored without pivoting and applied as
                             one block reflector, and the sketch is updated as Y2 -= Y1 R11^{-1} R12.
@@ -432,6 +439,10 @@ int mps_selftest_gemm(int M, int N, int K, int a_row, int a_conj, int a_mask, in
 
 /* Library version (major*10000 + minor*100 + patch). */
 int mps_version(void);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -65,8 +65,9 @@ def sketch_signs(rows, m, seed):
     return np.where(bits.reshape(rows, m) == 1, -1.0, 1.0).astype(np.complex128)
 
 
-def rqrcp(a, kmax=None, seed=0, nb=32, oversample=8, omega=None, keep_sketches=False):
-    """Truncated RQRCP of ``a`` (m x n).  Returns a dict with ``q`` (m x k), ``r`` (k x n,
+def rqrcp(a, kmax=None, seed=0, nb=64, oversample=8, omega=None, keep_sketches=False):
+    """Truncated RQRCP of ``a`` (m x n), blocks of ``nb`` pivots and an ``nb + oversample``
+    row sketch (defaults: 64 and 8, the GPU library's blocks of two 32-column panels).  Returns a dict with ``q`` (m x k), ``r`` (k x n,
     columns in pivoted order), ``jpvt`` (jpvt[t] = original column at position t),
     ``discarded`` (||A[k:, k:]||_F^2), and with ``keep_sketches`` the sketch and the
     column order after every block.  ``omega`` replaces the sketching matrix (any l x m)."""

@@ -41,7 +41,10 @@ def headers():
 
 
 def _compile(src, obj, extra):
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # hidden visibility: only the C ABI of include/mps.h is exported, so two builds
+    # loaded into one process (the checked and the plain library) share no symbol
+    # (function-local statics of templates would otherwise be unified across them)
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
            "-I", os.path.join(ROOT, "include"), *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -235,7 +235,10 @@ void gate_to_T(const mps_c128* g, int count, T* out) {
 #define CKE(x)                               \
   do {                                       \
     cudaError_t e_ = (x);                    \
-    if (e_ != cudaSuccess) return e_;        \
+    if (e_ != cudaSuccess) {                 \
+      note_cuda_failure(__FILE__, __LINE__); \
+      return e_;                             \
+    }                                        \
   } while (0)
 
 // The two-site gate pipeline on raw device pointers (Sec. III-C.2):
@@ -336,17 +339,17 @@ SkLayout sk_layout(size_t esz, int mmax, int nmax, int nb) {
     off = align_up(off + std::max<size_t>(bytes, 1));
     return o;
   };
-  L.lsk = nb + kSketchOversample;
+  L.lsk = 2 * nb + kSketchOversample;  // a block of two panels, plus oversampling
   L.ldy = (L.lsk + 3) / 4 * 4;
   const size_t mm = (size_t)std::max(mmax, 1), nn = (size_t)std::max(nmax, 1);
   L.Om = take(esz * L.ldy * mm);
   L.Ys = take(esz * L.ldy * nn);
-  L.Yw = take(esz * L.ldy * nn);
-  L.Ssk = take(esz * L.ldy * nb);
-  L.tau = take(esz * nb);
-  L.Wg = take(16 * (size_t)nb * nb);
-  L.jpvt = take(4 * nn);
-  L.seq = take(4 * (size_t)nb);
+  L.Yw = take(1);
+  L.Ssk = take(esz * L.ldy * 2 * nb);
+  L.tau = take(1);
+  L.Wg = take(1);
+  L.jpvt = take(1);
+  L.seq = take(4 * 2 * (size_t)nb);
   L.total = off;
   return L;
 }
@@ -567,8 +570,24 @@ int fail(mps_t h, int code, const std::string& m) {
   return code;
 }
 
+thread_local const char* t_fail_file = nullptr;  // innermost failing call of this thread
+thread_local int t_fail_line = 0;
+
+}  // namespace
+
+void mpsg::note_cuda_failure(const char* file, int line) {
+  if (t_fail_file) return;  // the innermost site was recorded first
+  const char* slash = std::strrchr(file, '/');
+  t_fail_file = slash ? slash + 1 : file;
+  t_fail_line = line;
+}
+
+namespace {
+
 int cuda_fail(mps_t h, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (t_fail_file) m += std::string(" (at ") + t_fail_file + ":" + std::to_string(t_fail_line) + ")";
+  t_fail_file = nullptr;
   return fail(h, e == cudaErrorMemoryAllocation ? MPS_E_NOMEM : MPS_E_CUDA, m);
 }
 
@@ -810,9 +829,9 @@ cudaError_t tune_split(const Ws<T>& w, const Knobs& base, int cl, int cm, int cr
 template <typename T>
 int tuned_knobs(mps_t h, int i, const T* gt, int chi, const SketchRef* sk, Knobs* kn) {
   *kn = h->kn;
-  if (!h->tune || h->trunc == MPS_TRUNC_SVD) return MPS_OK;
+  if (!h->tune || h->trunc != MPS_TRUNC_QRCP) return MPS_OK;  // the QP3 split only
   const int cl = h->bond[i], cm = h->bond[i + 1], cr = h->bond[i + 2];
-  if (h->kn.small && h->trunc == MPS_TRUNC_QRCP && small_gate_fits(cl, cm, cr)) return MPS_OK;  // one CTA: no knobs
+  if (h->kn.small && small_gate_fits(cl, cm, cr)) return MPS_OK;  // one CTA: no knobs
   const int m = 2 * cl, n = 2 * cr, k = std::min(std::min(m, n), chi);
   TuneEntry e;
   bool have = false;

@@ -69,6 +69,11 @@ struct GemmDesc {
   T* wk = nullptr;
 };
 
+// Records where a CUDA call first failed on this host thread (file name and line),
+// so that the error message of the library call that reports it names the site;
+// the report clears the record.
+void note_cuda_failure(const char* file, int line);
+
 template <typename T>
 cudaError_t gemm_simt(const GemmDesc<T>& d, cudaStream_t s);
 // number of kernel launches gemm_simt makes for this descriptor
@@ -183,21 +188,23 @@ struct QrPlan {
   bool use_tc = false;     // complex64 GEMMs on the tensor cores
   // pivot == 2: pivots chosen on a random sketch (blocked randomized QRCP); the
   // sketch scratch below is then required
-  int lsk = 0;              // sketch rows (nb + oversampling)
+  int lsk = 0;              // sketch rows (2 nb + oversampling)
   int64_t ldy = 0;          // leading dimension of Om, Ys, Yw, Ssk (>= lsk, multiple of 4)
   T* Om = nullptr;          // ldy x m: sketching matrix (+-1)
   T* Ys = nullptr;          // ldy x n: sketch, columns in the current order of W
   T* Yw = nullptr;          // ldy x n: copy factored to choose one block's pivots
-  T* Ssk = nullptr;         // ldy x nb: Y_sel R11^{-1}
+  T* Ssk = nullptr;         // ldy x 2 nb: Y_sel R11^{-1}
   T* sk_tau = nullptr;      // nb: reflector scalars of the sketch panel
   c128* sk_Wg = nullptr;    // nb x nb: w vectors of the sketch panel
   int* sk_jpvt = nullptr;   // n: column order of the sketch panel
-  int* piv_seq = nullptr;   // nb: position taken at each step of the sketch panel
+  int* piv_seq = nullptr;   // 2 nb: position taken at each step of a block's pivot choice
   unsigned long long seed = 0;  // generator state of the sketching matrix
 };
 
-// sketch rows beyond the block size (oversampling) of the randomized QRCP
+// randomized QRCP: a block of pivots is two panels (2 nb, at most kSketchBlockMax
+// columns) and the sketch has the block size plus kSketchOversample rows
 constexpr int kSketchOversample = 8;
+constexpr int kSketchBlockMax = 64;
 
 // ---------------------------------------------------------------------------
 // Small two-site gates (small_gate.cu): theta of at most kSmallDim x kSmallDim

@@ -628,7 +628,15 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     if (a.bulk && lane == 0) fence_proxy_async();  // generic writes before the barrier -> async reads
     bool xseen = false;
     bool pre = false;  // bulk mode: this batch's first two items were issued during the previous one
-    for (int cb = c0; cb < c1; cb += nbc) {
+    // The sweep direction alternates from step to step (batches, and the (column,
+    // chunk) items inside a batch): the columns one step reads last are still in L2
+    // when the next step starts, so part of each sweep is served from L2.  Every
+    // chunk sum lands in its own slot and is combined in a fixed order, so the
+    // results do not depend on the direction.
+    const bool rev = (kk & 1) != 0;
+    const int nbat = c1 > c0 ? (c1 - c0 + nbc - 1) / nbc : 0;
+    for (int bq = 0; bq < nbat; ++bq) {
+      const int cb = c0 + (rev ? nbat - 1 - bq : bq) * nbc;
       const int nc = min(nbc, c1 - cb);
       // D1: chunk sums
       if (a.bulk) {
@@ -647,7 +655,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           const int nit0 = nc0 * nchb;
           const int nli0 = (dw >= 0 && nit0 > dw) ? (nit0 - dw + kNDW - 1) / kNDW : 0;
           for (int li = 0; li < min(2, nli0); ++li) {
-            const int it = dw + kNDW * li, cl = it / nchb, ch = it - cl * nchb;
+            const int ir = dw + kNDW * li, it = rev ? nit0 - 1 - ir : ir, cl = it / nchb, ch = it - cl * nchb;
             const int cs = xbase + ch * CR, ce = min(m, cs + CR);
             const uint32_t mb = smem_u32(&s_mbar[warp][li]);
             mbar_expect_tx(mb, (uint32_t)((ce - cs) * sizeof(T)));
@@ -659,7 +667,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         pre = false;
         for (int li = 0; li < nli; ++li) {
           const int q = li & 1;
-          const int it = dw + kNDW * li, cl = it / nchb, ch = it - cl * nchb;
+          const int ir = dw + kNDW * li, it = rev ? nit - 1 - ir : ir, cl = it / nchb, ch = it - cl * nchb;
           const int cs = xbase + ch * CR, ce = min(m, cs + CR);
           const uint32_t mb = smem_u32(&s_mbar[warp][q]);
           const uint32_t par = (ph >> q) & 1u;
@@ -671,7 +679,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           if (lane == 0) s_dp[cl * nchb + ch] = s;
           __syncwarp();
           if (lane == 0 && li + 2 < nli) {
-            const int it2 = it + 2 * kNDW, cl2 = it2 / nchb, ch2 = it2 - cl2 * nchb;
+            const int ir2 = ir + 2 * kNDW, it2 = rev ? nit - 1 - ir2 : ir2, cl2 = it2 / nchb, ch2 = it2 - cl2 * nchb;
             const int cs2 = xbase + ch2 * CR, ce2 = min(m, cs2 + CR);
             // the slot's previous contents were consumed above (values in registers,
             // __syncwarp passed), so the copy cannot overtake those reads
@@ -682,13 +690,14 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         }
         // every slot of this warp is free again: start the next batch's copies now,
         // so they are in flight during this batch's epilogue
-        if (cb + nbc < c1) {
-          if (lane == 0) prologue(cb + nbc, min(nbc, c1 - cb - nbc));
+        if (bq + 1 < nbat) {
+          const int cbn = c0 + (rev ? nbat - 2 - bq : bq + 1) * nbc;
+          if (lane == 0) prologue(cbn, min(nbc, c1 - cbn));
           pre = true;
         }
       } else {
-        for (int it = warp; it < nc * nch; it += PNW) {
-          const int cl = it / nch, ch = it - cl * nch;
+        for (int ir = warp; ir < nc * nch; ir += PNW) {
+          const int it = rev ? nc * nch - 1 - ir : ir, cl = it / nch, ch = it - cl * nch;
           const int t = cb + cl;
           const int r0 = max(J + 1, xbase + ch * chr), r1 = min(m, xbase + (ch + 1) * chr);
           const T* col = W + (int64_t)t * ldw;
@@ -1318,7 +1327,10 @@ static cudaError_t panel_setup(int& max_blocks) {
 #define CK(x)                                  \
   do {                                         \
     cudaError_t e_ = (x);                      \
-    if (e_ != cudaSuccess) return e_;          \
+    if (e_ != cudaSuccess) {                   \
+      note_cuda_failure(__FILE__, __LINE__);   \
+      return e_;                               \
+    }                                          \
   } while (0)
 
 // Launch accounting of one QR: either by kernel class, or everything under
@@ -1712,7 +1724,7 @@ __global__ void sketch_omega_kernel(T* Om, int64_t ldy, int lsk, int m, unsigned
 template <typename T>
 __global__ void apply_swaps_kernel(T* A, int64_t lda, int rows, int j0, const int* seq, int kb, int* jpvt, int nc,
                                    int* err) {
-  __shared__ int s_seq[kPanelNbMax];
+  __shared__ int s_seq[kSketchBlockMax];
   if (threadIdx.x < kb) {
     const int q = seq[threadIdx.x];
     // a position outside [t, nc) would be an out-of-range column: the swap is skipped
@@ -1741,26 +1753,22 @@ __global__ void apply_swaps_kernel(T* A, int64_t lda, int rows, int j0, const in
 }
 
 // S (ldy x kb, rows < lsk) with S R11 = Y[:, j0:j0+kb], R11 = W[j0:j0+kb, j0:j0+kb]
-// upper triangular, by forward substitution per sketch row; a diagonal entry whose
-// squared modulus is below the smallest normal number of the data type (a column
-// with no residual) contributes nothing (its column of S is zero).
+// upper triangular (read from W: every thread reads the same entries), by forward
+// substitution per sketch row; a diagonal entry whose squared modulus is below the
+// smallest normal number of the data type (a column with no residual) contributes
+// nothing (its column of S is zero).
 template <typename T>
 __global__ void sketch_solve_kernel(const T* Ys, int64_t ldy, int lsk, int j0, int kb, const T* W, int64_t ldw,
                                     T* S) {
   using R = typename real_of<T>::type;
-  __shared__ T r11[kPanelNbMax][kPanelNbMax + 1];
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int i = e % kb, j = e / kb;
-    r11[i][j] = i <= j ? W[j0 + i + (int64_t)(j0 + j) * ldw] : mk<R>(0, 0);
-  }
-  __syncthreads();
   const double tiny = sizeof(R) == 8 ? 2.2250738585072014e-308 : 1.1754943508222875e-38;
   for (int i = threadIdx.x; i < lsk; i += blockDim.x) {
-    T sv[kPanelNbMax];
+    T sv[kSketchBlockMax];
     for (int c = 0; c < kb; ++c) {
       T rhs = Ys[i + (int64_t)(j0 + c) * ldy];
-      for (int t = 0; t < c; ++t) rhs = rhs - sv[t] * r11[t][c];
-      const T d = r11[c][c];
+      const T* rc = W + j0 + (int64_t)(j0 + c) * ldw;  // column c of R11
+      for (int t = 0; t < c; ++t) rhs = rhs - sv[t] * rc[t];
+      const T d = rc[c];
       const double d2 = (double)d.re * (double)d.re + (double)d.im * (double)d.im;
       T q = mk<R>(0, 0);
       if (d2 >= tiny) {
@@ -2049,8 +2057,7 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
   const ClassMap K{p.kclass};
   const int m = p.m, n = p.n, k = p.k, nb = p.nb, l = p.lsk;
   const int64_t ldy = p.ldy;
-  if (!p.Om || !p.Ys || !p.Yw || !p.Ssk || !p.sk_tau || !p.sk_Wg || !p.sk_jpvt || !p.piv_seq || l < nb ||
-      ldy < l)
+  if (!p.Om || !p.Ys || !p.Ssk || !p.piv_seq || l < 2 * nb || ldy < l || 2 * nb > kSketchBlockMax)
     return cudaErrorInvalidValue;
   int maxb = 1;
   CK(panel_setup<T>(maxb));
@@ -2084,76 +2091,94 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
     CK(gemm_simt<T>(d, s));
     hook_after(hooks, K(MPS_KCLASS_OTHER), 2 + gemm_launches(d));
   }
-  for (int pi = 0; pi < npanels; ++pi) {
-    const int j0 = pi * nb;
-    const int kb = std::min(nb, k - j0);
-    const int J1 = j0 + kb;
+  const int bw = 2 * nb;  // pivots per sketch block: two panels, one block reflector
+  for (int j0 = 0; j0 < k; j0 += bw) {
+    const int kbb = std::min(bw, k - j0);
+    const int kb0 = std::min(nb, kbb), kb1 = kbb - kb0;
+    const int pi0 = j0 / nb;
+    const int J1 = j0 + kbb;
     const int nr = n - j0;
     // a. the block's pivots from the sketch's remaining columns (sketch_pivots_kernel),
     //    then the same column swaps on W, on the sketch and on jpvt
-    hook_before(hooks, K(MPS_KCLASS_PANEL), (double)l * nr * sizeof(T), 8.0 * l * nr * kb);
-    CK(launch_sketch_pivots<T>(p.Ys + (int64_t)j0 * ldy, ldy, l, nr, kb, p.piv_seq, reinterpret_cast<int*>(p.vn1),
+    hook_before(hooks, K(MPS_KCLASS_PANEL), (double)l * nr * sizeof(T), 8.0 * l * nr * kbb);
+    CK(launch_sketch_pivots<T>(p.Ys + (int64_t)j0 * ldy, ldy, l, nr, kbb, p.piv_seq, reinterpret_cast<int*>(p.vn1),
                                p.SK, p.sk_cap, p.bar, p.err, p.barrier_extra, p.timeout_ns, p.flag_tol, s));
     apply_swaps_kernel<T><<<std::max(1, std::min(1024, (m + 255) / 256)), 256, 0, s>>>(p.W, p.ldw, m, j0, p.piv_seq,
-                                                                                      kb, p.jpvt, nr, p.err);
+                                                                                      kbb, p.jpvt, nr, p.err);
     CK(cudaGetLastError());
-    apply_swaps_kernel<T><<<1, 256, 0, s>>>(p.Ys, ldy, l, j0, p.piv_seq, kb, nullptr, nr, p.err);
+    apply_swaps_kernel<T><<<1, 256, 0, s>>>(p.Ys, ldy, l, j0, p.piv_seq, kbb, nullptr, nr, p.err);
     CK(cudaGetLastError());
     hook_after(hooks, K(MPS_KCLASS_PANEL), 3);
-    PanelArgs<T> a;
-    a.F = p.F;
-    a.vn1 = p.vn1;
-    a.vn2 = p.vn2;
-    a.red_norm = p.red_norm;
-    a.red_w = reinterpret_cast<T*>(p.red_w);
-    a.red_argv = reinterpret_cast<long long*>(p.red_argv);
-    a.red_argi = p.red_argi;
-    a.alpha_slot = p.alpha_slot;
-    a.bar = p.bar;
-    a.err = p.err;
-    a.timeout_ns = p.timeout_ns;
-    a.flag_tol = p.flag_tol;
-    a.nb = nb;
-    a.kb = kb;
-    // b. the block without pivoting (as a centre move's panel)
-    PanelArgs<T> b = a;
+    // b. the block's two panels without pivoting (as a centre move's): the first
+    //    panel's reflector is applied to the second panel's columns only
+    PanelArgs<T> b;
+    b.F = p.F;
+    b.vn1 = p.vn1;
+    b.vn2 = p.vn2;
+    b.red_norm = p.red_norm;
+    b.red_w = reinterpret_cast<T*>(p.red_w);
+    b.red_argv = reinterpret_cast<long long*>(p.red_argv);
+    b.red_argi = p.red_argi;
+    b.alpha_slot = p.alpha_slot;
+    b.bar = p.bar;
+    b.err = p.err;
+    b.timeout_ns = p.timeout_ns;
+    b.flag_tol = p.flag_tol;
+    b.nb = nb;
     b.W = p.W;
     b.ldw = p.ldw;
     b.m = m;
     b.n = n;
-    b.j0 = j0;
-    b.nend = J1;
     b.pivot = 0;
     b.jpvt = p.jpvt;
     b.tau = p.tau;
-    b.Tp = p.Tfac + (size_t)pi * nb * nb;
-    b.Wg = p.Wg + (size_t)pi * nb * nb;
     b.piv_seq = nullptr;
-    double bytes = 0.0, flops = 0.0;
-    for (int j = j0; j < J1; ++j) {
-      bytes += (double)(m - j) * (J1 - j) * sizeof(T);
-      flops += 8.0 * (m - j) * (J1 - j);
-    }
-    hook_before(hooks, K(MPS_KCLASS_PANEL), bytes, flops);
-    CK(launch_panel<T>(b, p.barrier_extra, gcap, true, s));
-    hook_after(hooks, K(MPS_KCLASS_PANEL), 1);
-    if (J1 < n) {
-      // the block reflector on every column to the right (rows j0..m)
+    for (int h = 0; h < 2; ++h) {
+      const int kbh = h == 0 ? kb0 : kb1;
+      if (kbh <= 0) break;
+      const int jh = j0 + h * nb, pih = pi0 + h;
+      b.j0 = jh;
+      b.kb = kbh;
+      b.nend = jh + kbh;
+      b.Tp = p.Tfac + (size_t)pih * nb * nb;
+      b.Wg = p.Wg + (size_t)pih * nb * nb;
+      double bytes = 0.0, flops = 0.0;
+      for (int j = jh; j < jh + kbh; ++j) {
+        bytes += (double)(m - j) * (jh + kbh - j) * sizeof(T);
+        flops += 8.0 * (m - j) * (jh + kbh - j);
+      }
+      hook_before(hooks, K(MPS_KCLASS_PANEL), bytes, flops);
+      CK(launch_panel<T>(b, p.barrier_extra, gcap, true, s));
+      hook_after(hooks, K(MPS_KCLASS_PANEL), 1);
       int nl = 1;
-      const double M = m - j0, N = n - J1;
-      hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * kb + 3.0 * M * N) * sizeof(T), 16.0 * M * N * kb);
-      tfactor_kernel<T><<<1, 1024, 0, s>>>(p.Wg, p.tau, pi, k, nb, p.Tfac);
+      hook_before(hooks, K(MPS_KCLASS_UPDATE), 0, 0);
+      tfactor_kernel<T><<<1, 1024, 0, s>>>(p.Wg, p.tau, pih, k, nb, p.Tfac);
       CK(cudaGetLastError());
-      CK(apply_block<T>(p, j0, kb, p.Tfac + (size_t)pi * nb * nb, nb, 1, p.W, p.ldw, J1, n - J1, &nl, s));
+      if (h == 0 && kb1 > 0)
+        CK(apply_block<T>(p, j0, kb0, p.Tfac + (size_t)pi0 * nb * nb, nb, 1, p.W, p.ldw, j0 + kb0, kb1, &nl, s));
       hook_after(hooks, K(MPS_KCLASS_UPDATE), nl);
+    }
+    // the block's reflector: both panels' T factors merged into one (the outer
+    // factor, also used to form Q), applied to every column to the right
+    {
+      int nl = 0, kbm = 0;
+      const double M = m - j0, N = n - J1;
+      hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * kbb + 3.0 * M * N) * sizeof(T), 16.0 * M * N * kbb);
+      CK(outer_tfactor<T>(p, pi0, &kbm, &nl, s));
+      CK(apply_block<T>(p, j0, kbm, p.Tblk + (size_t)(pi0 / 2) * 4 * nb * nb, 2 * nb, 1, p.W, p.ldw, J1, n - J1, &nl,
+                        s));
+      hook_after(hooks, K(MPS_KCLASS_UPDATE), nl);
+    }
+    if (J1 < n) {
       // c. sketch update Y[:, J1:] -= (Y[:, j0:J1] R11^{-1}) R12
-      hook_before(hooks, K(MPS_KCLASS_OTHER), (double)(l + kb) * N * sizeof(T) * 2, 8.0 * l * kb * N);
-      sketch_solve_kernel<T><<<1, 64, 0, s>>>(p.Ys, ldy, l, j0, kb, p.W, p.ldw, p.Ssk);
+      const double N = n - J1;
+      hook_before(hooks, K(MPS_KCLASS_OTHER), (double)(l + kbb) * N * sizeof(T) * 2, 8.0 * l * kbb * N);
+      sketch_solve_kernel<T><<<1, 128, 0, s>>>(p.Ys, ldy, l, j0, kbb, p.W, p.ldw, p.Ssk);
       CK(cudaGetLastError());
       GemmDesc<T> d;
       d.M = l;
       d.N = n - J1;
-      d.K = kb;
+      d.K = kbb;
       d.alpha = mk<R>(-1, 0);
       d.beta = mk<R>(1, 0);
       d.A = p.Ssk;
@@ -2167,18 +2192,6 @@ cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* 
       CK(gemm_simt<T>(d, s));
       hook_after(hooks, K(MPS_KCLASS_OTHER), 2);
     }
-  }
-  {
-    // triangular factors for Q formation: every panel's, then the outer blocks
-    int nl = 1;
-    hook_before(hooks, K(MPS_KCLASS_FORMQ), 0, 0);
-    tfactor_kernel<T><<<npanels, 1024, 0, s>>>(p.Wg, p.tau, 0, k, nb, p.Tfac);
-    CK(cudaGetLastError());
-    for (int pb = 0; pb < npanels; pb += 2) {
-      int kbb = 0;
-      CK(outer_tfactor<T>(p, pb, &kbb, &nl, s));
-    }
-    hook_after(hooks, K(MPS_KCLASS_FORMQ), nl);
   }
   if (p.discarded) {
     // discarded = ||W[k:m, k:n]||_F^2

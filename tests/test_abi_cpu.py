@@ -41,6 +41,27 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+@pytest.mark.parametrize("checked", [False, True])
+def test_library_exports_only_the_c_abi(checked):
+    """Both builds export the header's functions and no function-local static of the
+    library's own code: a GNU-unique symbol (such a static of a template) would be one
+    object for every build loaded into a process, so the second library would skip its
+    own once-per-device setup (a kernel attribute) and its launch would fail."""
+    import shutil
+    import subprocess
+
+    from paper_2505_06119_gb300 import build
+
+    if not shutil.which("nm"):
+        pytest.skip("nm not installed")
+    path = build.build(checked=checked)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    syms = [line.split() for line in out.splitlines() if len(line.split()) == 3]
+    assert not [s for s in syms if s[1] == "u"]
+    text = {s[2] for s in syms if s[1] == "T"}
+    assert text == set(declared_functions())
+
+
 def test_binding_covers_every_declared_symbol():
     from paper_2505_06119_gb300 import _lib
 
