@@ -152,12 +152,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# DRAM traffic of the panel kernel from one ncu capture (profiles/qr_panel_kernel_chi2048.md):
-# dram bytes / algorithmic bytes of the captured launch.  Traffic scales with the
-# algorithmic bytes (both are sums over the trailing block), so a launch's traffic is
-# this ratio times its algorithmic bytes.  Valid only for the kernel source it was
-# measured on (sha256 of the qr_panel_kernel definition in csrc/qr.cu); otherwise null.
-PANEL_NCU = {"kernel_sha256": None, "dram_over_algorithmic": None}
+# DRAM traffic of the panel kernel from one ncu capture (profiles/qr_panel_kernel_chi4096.md):
+# the dram bytes of all 128 panel launches of one chi = 4096 gate over their algorithmic
+# bytes.  The sweep's L2 reuse makes the ratio depend on the bond dimension (the share
+# of the trailing matrix that stays in L2), so it is used only at the chi it was
+# measured at, and only for the kernel source it was measured on (sha256 of the
+# qr_panel_kernel definition in csrc/qr.cu); otherwise the traffic is null.
+PANEL_NCU = {"kernel_sha256": "683989a27d7efaac9c93e84600cfcd46d542e38dd3e972c1952180cc7b5bc3b0", "chi": 4096,
+             "dram_over_algorithmic": 0.7414}
 
 
 def panel_kernel_source():
@@ -170,8 +172,11 @@ def panel_kernel_source():
     return src[start:end]
 
 
-def panel_traffic(alg_bytes_per_launch):
+def panel_traffic(alg_bytes_per_launch, chi):
     import hashlib
+
+    if chi != PANEL_NCU["chi"]:
+        return None
 
     try:
         sha = hashlib.sha256(panel_kernel_source().encode()).hexdigest()
@@ -288,7 +293,7 @@ def ours(args):
         "roofline": {"bound": "hbm", "kernel": "qr_panel_kernel (pivoted-QR panel: per-step trailing GEMV)",
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / peaks.get("hbm_gbs", 1.0),
-                     "traffic": panel_traffic(panel["alg_bytes"] / max(1, panel["launches"])),
+                     "traffic": panel_traffic(panel["alg_bytes"] / max(1, panel["launches"]), chi),
                      "traffic_unit": "bytes per launch",
                      "peak_source": peak_src,
                      "launches_timed": panel["launches"], "kernel_ms_per_step": panel["ms"] / args.steps},

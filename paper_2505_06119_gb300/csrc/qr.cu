@@ -85,6 +85,7 @@ struct PanelArgs {
   int xcap;    // elements of x that fit in dynamic shared memory
   int xs_off;  // byte offset of the x vector in dynamic shared memory
   int bulk;    // phase D streams column chunks with bulk asynchronous copies
+  int keep;    // bulk mode: chunks per CTA and step read under the L2 keep policy
   int* piv_seq;  // optional: the pivot position p taken at each step
 };
 
@@ -351,6 +352,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     mbar_init(smem_u32(&s_mbar[warp][1]), 1);
     if (warp == 0) mbar_init(smem_u32(&s_xbar), 1);
   }
+  const uint64_t pol_keep = l2_policy_keep(), pol_stream = l2_policy_stream();
   unsigned ph = 0;   // bulk mode: parity of the next completion of this warp's slots
   unsigned xph = 0;  // bulk mode: parity of the next completion of the x copy
   __syncthreads();
@@ -632,9 +634,17 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     // chunk) items inside a batch): the columns one step reads last are still in L2
     // when the next step starts, so part of each sweep is served from L2.  Every
     // chunk sum lands in its own slot and is combined in a fixed order, so the
-    // results do not depend on the direction.
+    // results do not depend on the direction.  In bulk mode the last a.keep chunks
+    // of this CTA's traversal (the first ones of the next step's) are read under the
+    // L2 keep policy and the others under the stream policy, so that the lines the
+    // next step will read first are the last to be evicted.
     const bool rev = (kk & 1) != 0;
     const int nbat = c1 > c0 ? (c1 - c0 + nbc - 1) / nbc : 0;
+    const int bfull = nbc * nchb;                                             // chunks of a full batch
+    const int blast = nbat > 0 ? (c1 - c0 - (nbat - 1) * nbc) * nchb : 0;  // of the last (first when rev)
+    const int keep_from = (c1 - c0) * nchb - a.keep;  // traversal position of the first kept chunk
+    // chunks of the batches before traversal position q
+    auto before = [&](int q) { return rev ? (q == 0 ? 0 : blast + (q - 1) * bfull) : q * bfull; };
     for (int bq = 0; bq < nbat; ++bq) {
       const int cb = c0 + (rev ? nbat - 1 - bq : bq) * nbc;
       const int nc = min(nbc, c1 - cb);
@@ -651,7 +661,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           xseen = true;
         }
         // first two items of batch cb0 (nc0 columns) into slots 0 and 1
-        auto prologue = [&](int cb0, int nc0) {
+        auto prologue = [&](int cb0, int nc0, int base0) {
           const int nit0 = nc0 * nchb;
           const int nli0 = (dw >= 0 && nit0 > dw) ? (nit0 - dw + kNDW - 1) / kNDW : 0;
           for (int li = 0; li < min(2, nli0); ++li) {
@@ -659,11 +669,12 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
             const int cs = xbase + ch * CR, ce = min(m, cs + CR);
             const uint32_t mb = smem_u32(&s_mbar[warp][li]);
             mbar_expect_tx(mb, (uint32_t)((ce - cs) * sizeof(T)));
-            bulk_g2s(smem_u32(slot0 + li * kSlot), W + (int64_t)(cb0 + cl) * ldw + cs,
-                     (uint32_t)((ce - cs) * sizeof(T)), mb);
+            bulk_g2s_hint(smem_u32(slot0 + li * kSlot), W + (int64_t)(cb0 + cl) * ldw + cs,
+                          (uint32_t)((ce - cs) * sizeof(T)), mb, base0 + ir >= keep_from ? pol_keep : pol_stream);
           }
         };
-        if (lane == 0 && !pre) prologue(cb, nc);
+        const int base = before(bq);
+        if (lane == 0 && !pre) prologue(cb, nc, base);
         pre = false;
         for (int li = 0; li < nli; ++li) {
           const int q = li & 1;
@@ -684,15 +695,15 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
             // the slot's previous contents were consumed above (values in registers,
             // __syncwarp passed), so the copy cannot overtake those reads
             mbar_expect_tx(mb, (uint32_t)((ce2 - cs2) * sizeof(T)));
-            bulk_g2s(smem_u32(slot0 + q * kSlot), W + (int64_t)(cb + cl2) * ldw + cs2,
-                     (uint32_t)((ce2 - cs2) * sizeof(T)), mb);
+            bulk_g2s_hint(smem_u32(slot0 + q * kSlot), W + (int64_t)(cb + cl2) * ldw + cs2,
+                          (uint32_t)((ce2 - cs2) * sizeof(T)), mb, base + ir2 >= keep_from ? pol_keep : pol_stream);
           }
         }
         // every slot of this warp is free again: start the next batch's copies now,
         // so they are in flight during this batch's epilogue
         if (bq + 1 < nbat) {
           const int cbn = c0 + (rev ? nbat - 2 - bq : bq + 1) * nbc;
-          if (lane == 0) prologue(cbn, min(nbc, c1 - cbn));
+          if (lane == 0) prologue(cbn, min(nbc, c1 - cbn), before(bq + 1));
           pre = true;
         }
       } else {
@@ -1264,6 +1275,19 @@ int num_sms() {
   });
 }
 
+// L2 capacity of the current device in bytes (0 when it cannot be read)
+static PerDevice g_l2;
+static int l2_bytes() {
+  return (int)g_l2.get([]() -> long long {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;  // not cached: the next call asks again
+    }
+    return std::max(n, 0);
+  });
+}
+
 constexpr int kPanelSmem = 200 * 1024;  // dynamic shared memory of the panel kernel
 
 constexpr int kCPanelSmem = 200 * 1024;
@@ -1476,12 +1500,16 @@ static cudaError_t launch_panel(PanelArgs<T>& a, unsigned barrier_extra, int gca
     dyn = kRing + (fits ? (int)xb : 0);
     a.xs_off = kRing;
     a.xcap = fits ? (int)(xb / (int64_t)sizeof(T)) : 0;
+    // three quarters of L2 hold the chunks each step reads last (the rest keeps
+    // x, F and the reduction slots)
+    a.keep = (int)std::min<int64_t>(1 << 30, (int64_t)std::max(0, l2_bytes()) * 3 / 4 / ((int64_t)G * kSlot));
   } else {
     // dynamic shared memory sized to the x vector this panel stages (rounded
     // to 16 KB): the rest of the SM's unified L1/shared storage stays L1,
     // which holds the trailing sweep's loads in flight
     const int need = (int)std::min<int64_t>((int64_t)(m - j0 + 2) * sizeof(T), smem);
     dyn = std::min(smem, (need + 16383) / 16384 * 16384);
+    a.keep = 0;
     a.xs_off = 0;
     a.xcap = dyn / (int)sizeof(T);
   }
