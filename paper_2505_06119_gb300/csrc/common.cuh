@@ -163,6 +163,42 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, i
   return s_ok != 0;
 }
 
+// The same barrier for a kernel that read the generation word once at its start
+// (thread 0, before its first arrival; the word only advances once every CTA has
+// arrived, so that value is current) and tracks it in `gen` (thread 0's copy):
+// one round trip to global memory less per barrier.
+__device__ __forceinline__ bool grid_barrier_g(unsigned* bar, unsigned expected, int* err,
+                                               unsigned long long timeout_ns, unsigned& gen) {
+  __shared__ int s_okg;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned arrived = atom_add_acqrel_u32(&bar[0], 1u);
+    if (arrived == expected - 1) {
+      st_relaxed_u32(&bar[0], 0u);
+      st_release_u32(&bar[1], gen + 1);
+    } else {
+      unsigned long long t0 = globaltimer_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(&bar[1]) == gen) {
+        if (ld_relaxed_i32(err) != DEV_OK) {
+          ok = 0;
+          break;
+        }
+        if ((++spins & 63u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
+          atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    gen += 1;
+    s_okg = ok;
+  }
+  __syncthreads();
+  return s_okg != 0;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {

@@ -335,6 +335,9 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   __shared__ T s_vrow[kPanelNbMax];   // W[J, j0+i]
   __shared__ T s_wp[PNW][kPanelNbMax];  // per-warp partials of V^H x (phase B)
   __shared__ T s_dp[kDpCap];  // phase-D chunk sums
+  __shared__ T s_wn[kDBatch];                         // D2: updated row-J entries of the batch
+  __shared__ double s_v1[kDBatch], s_v2[kDBatch];    // D2: squared norms (current, last exact)
+  __shared__ int s_need[kDBatch];                     // D2: exact recompute flags
   __shared__ int s_bi;
   __shared__ c128 s_scal[3];  // tau, 1/(alpha-beta), beta
 
@@ -346,7 +349,11 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   // an earlier bounded wait expired: the factorisation is void, leave at once
   // (decided once for the whole CTA)
   __shared__ int s_skip;
-  if (tid == 0) s_skip = ld_relaxed_i32(a.err) != DEV_OK;
+  unsigned bgen = 0;  // thread 0: generation of the grid barrier (grid_barrier_g)
+  if (tid == 0) {
+    s_skip = ld_relaxed_i32(a.err) != DEV_OK;
+    bgen = ld_acquire_u32(&a.bar[1]);
+  }
   if (a.bulk && lane == 0) {
     mbar_init(smem_u32(&s_mbar[warp][0]), 1);
     mbar_init(smem_u32(&s_mbar[warp][1]), 1);
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       a.red_argv[b] = bv;
       a.red_argi[b] = bi;
     }
-    if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
+    if (!grid_barrier_g(a.bar, a.expected, a.err, a.timeout_ns, bgen)) return;
   }
 
   c128 s_prev = mk<double>(0, 0);
@@ -435,15 +442,16 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     }
     T* colJ = W + (int64_t)J * ldw;
     T* colP = W + (int64_t)p * ldw;
-    // ---------------- B1: swap rows above J (any CTA)
-    if (p != J) {
-      int s0, s1;
-      split_range(0, J, G, b, s0, s1);
-      for (int r = s0 + tid; r < s1; r += PNT) {
-        T t0 = colJ[r];
-        colJ[r] = colP[r];
-        colP[r] = t0;
-      }
+    // ---------------- B1: swap rows above J (any CTA).  The first PNT rows of this
+    // CTA's share are loaded here and stored after the B2 row loop, so that their
+    // round trip overlaps B2's loads (the rows are disjoint from B2's).
+    int s0 = 0, s1 = 0;
+    if (p != J) split_range(0, J, G, b, s0, s1);
+    const bool b1 = s0 + tid < s1;
+    T b1j = mk<R>(0, 0), b1p = mk<R>(0, 0);
+    if (b1) {
+      b1j = colJ[s0 + tid];
+      b1p = colP[s0 + tid];
     }
     // ---------------- B2: rows [u0, u1) of J..m-1: swap, deferred scaling of the
     // previous reflector, column update x = W[:,J] - V F[p,:]^H, partial sums.
@@ -509,6 +517,10 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           for (int u = 0; u < U; ++u) cs[u] = cs[u] + cconj(vr[u]) * x;
         }
       }
+      if (b1) {
+        colJ[s0 + tid] = b1p;
+        colP[s0 + tid] = b1j;
+      }
       if (a.bulk && wrote) fence_proxy_async();  // these stores before the bulk reads of phase C/D
       // reduce over the 8 rows of the warp
 #pragma unroll
@@ -530,13 +542,22 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         a.red_w[(int64_t)b * nb + tid] = w;
       }
     }
+    if (b >= gb && b1) {
+      colJ[s0 + tid] = b1p;
+      colP[s0 + tid] = b1j;
+    }
+    for (int r = s0 + PNT + tid; r < s1; r += PNT) {  // shares of more than PNT rows (small grids)
+      T t0 = colJ[r];
+      colJ[r] = colP[r];
+      colP[r] = t0;
+    }
     if (b == 0 && tid == 0 && p != J) {
       int t0 = a.jpvt[J];
       a.jpvt[J] = a.jpvt[p];
       a.jpvt[p] = t0;
     }
     if (b == 0 && tid == 0 && a.piv_seq) a.piv_seq[kk] = p;
-    if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
+    if (!grid_barrier_g(a.bar, a.expected, a.err, a.timeout_ns, bgen)) return;
 
     // ---------------- C: reflector (every CTA, identical FP64 arithmetic).
     // Warp 0 computes beta, tau and 1/(alpha - beta) in FP64, then combines the
@@ -655,11 +676,6 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         const int nit = nc * nchb;
         const int nli = (dw >= 0 && nit > dw) ? (nit - dw + kNDW - 1) / kNDW : 0;  // this warp's items
         unsigned char* slot0 = smem_raw + warp * 2 * kSlot;
-        if (nli > 0 && xcopy && !xseen) {  // x staged by the bulk copy of phase C
-          if (!mbar_wait(smem_u32(&s_xbar), xph, a.err, a.timeout_ns))
-            mbar_wait_plain(smem_u32(&s_xbar), xph, a.timeout_ns);
-          xseen = true;
-        }
         // first two items of batch cb0 (nc0 columns) into slots 0 and 1
         auto prologue = [&](int cb0, int nc0, int base0) {
           const int nit0 = nc0 * nchb;
@@ -676,6 +692,13 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         const int base = before(bq);
         if (lane == 0 && !pre) prologue(cb, nc, base);
         pre = false;
+        // x (staged by the bulk copy of phase C) is waited for after the first chunk
+        // copies were issued, so that the two round trips overlap
+        if (nli > 0 && xcopy && !xseen) {
+          if (!mbar_wait(smem_u32(&s_xbar), xph, a.err, a.timeout_ns))
+            mbar_wait_plain(smem_u32(&s_xbar), xph, a.timeout_ns);
+          xseen = true;
+        }
         for (int li = 0; li < nli; ++li) {
           const int q = li & 1;
           const int ir = dw + kNDW * li, it = rev ? nit - 1 - ir : ir, cl = it / nchb, ch = it - cl * nchb;
@@ -743,17 +766,24 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           }
         }
       }
+      T fT[CPW];
 #pragma unroll
       for (int q = 0; q < CPW; ++q) {
         const int cl = warp + PNW * q;
+        fT[q] = mk<R>(0, 0);
         if (cl >= nc) continue;  // warp-uniform
         const int t = cb + cl;
-        const int src = (t == p) ? J : t;
-        const T* col = W + (int64_t)t * ldw;
-        const T* Fs = a.F + (int64_t)src * nb;
         T* Ft = a.F + (int64_t)t * nb;
+        // chunk sums in chunk order; eight shared-memory loads in flight at a time
         T acc = mk<R>(0, 0);
-        for (int ch = 0; ch < nchb; ++ch) acc = acc + s_dp[cl * nchb + ch];
+        for (int c8 = 0; c8 < nchb; c8 += 8) {
+          T dv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) dv[u] = c8 + u < nchb ? s_dp[cl * nchb + c8 + u] : mk<R>(0, 0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c8 + u < nchb) acc = acc + dv[u];
+        }
         const T wJt = wJtT[q];
         const T y = cconj(wJt) + sc * acc;
         // F[t, kk] = tau * (y - sum_i F[src, i] w_i); row update of W[J, t]
@@ -771,26 +801,54 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         rowu.im = warp_sum(rowu.im);
         const T f = tau * (y - fw);
         const T wnew = wJt - rowu - cconj(f);
-        double v1 = v1a[q], v2 = v2a[q];
-        int need = 0;
+        fT[q] = f;
         if (lane == 0) {
           Ft[kk] = cconj(f);
           W[J + (int64_t)t * ldw] = wnew;
-          if (a.pivot) {
-            if (L <= 0) {
-              v1 = 0.0;
-            } else if (v1 > 0.0) {
-              // FP64 downdate of the squared norm; recompute when it has lost accuracy
-              const double r2 = (double)wnew.re * (double)wnew.re + (double)wnew.im * (double)wnew.im;
-              const double c = fmax(v1 - r2, 0.0);
-              if (c <= a.flag_tol * v2)
-                need = 1;
-              else
-                v1 = c;
-            }
-          }
+          s_wn[cl] = wnew;
+          s_v1[cl] = v1a[q];
+          s_v2[cl] = v2a[q];
         }
-        need = __shfl_sync(0xffffffffu, need, 0);
+      }
+      // FP64 downdate of the squared norms, one column per lane of warp 0, so that the
+      // batch's FP64 arithmetic takes a handful of warp instructions; a column whose
+      // downdated norm has lost accuracy is flagged for an exact recompute
+      if (a.pivot) {
+        __syncthreads();
+        if (warp == 0 && lane < nc) {
+          double v1 = s_v1[lane];
+          int need = 0;
+          if (L <= 0) {
+            v1 = 0.0;
+          } else if (v1 > 0.0) {
+            const T wn = s_wn[lane];
+            const double r2 = (double)wn.re * (double)wn.re + (double)wn.im * (double)wn.im;
+            const double c = fmax(v1 - r2, 0.0);
+            if (c <= a.flag_tol * s_v2[lane])
+              need = 1;
+            else
+              v1 = c;
+          }
+          s_v1[lane] = v1;
+          s_need[lane] = need;
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        const int cl = warp + PNW * q;
+        if (cl >= nc) continue;  // warp-uniform
+        const int t = cb + cl;
+        const int src = (t == p) ? J : t;
+        const T* col = W + (int64_t)t * ldw;
+        const T* Fs = a.F + (int64_t)src * nb;
+        const T f = fT[q];
+        double v1 = 0.0, v2 = v2a[q];
+        int need = 0;
+        if (a.pivot) {
+          v1 = s_v1[cl];
+          need = s_need[cl];
+        }
         if (need) {
           // exact squared norm of the column after step J: rows > J of
           // W[:, t] - V[:, 0:kk] F[t, 0:kk]^H - (s x) conj(f)
@@ -849,7 +907,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     s_prev = s_scal[1];
     // (no proxy fence here: what this step wrote with plain stores, row J and the
     // panel's own columns, is not read by a bulk copy before the next phase-B fence)
-    if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
+    if (!grid_barrier_g(a.bar, a.expected, a.err, a.timeout_ns, bgen)) return;
   }
   // final deferred scaling of the panel's last reflector, rows > Jl
   if (a.kb > 0) {
@@ -1872,7 +1930,11 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
   __shared__ int s_win, s_wb;
   __shared__ c128 s_tau, s_sc;
   __shared__ int s_skip;
-  if (tid == 0) s_skip = ld_relaxed_i32(a.err) != DEV_OK;
+  unsigned bgen = 0;  // thread 0: generation of the grid barrier (grid_barrier_g)
+  if (tid == 0) {
+    s_skip = ld_relaxed_i32(a.err) != DEV_OK;
+    bgen = ld_acquire_u32(&a.bar[1]);
+  }
   for (int e = tid; e < l * nl; e += SKT) {
     const int c = e / l, r = e - c * l;  // coalesced reads along each column
     ys[r * nl + c] = a.Y[r + (int64_t)(c0 + c) * a.ldy];
@@ -1929,7 +1991,7 @@ __global__ void __launch_bounds__(SKT) sketch_pivots_kernel(SketchPivArgs<T> a) 
       const int c = s_bi[0] - c0;
       for (int r = tid; r < l; r += SKT) pub[2 + r] = ys[r * nl + c];
     }
-    if (!grid_barrier(a.bar, a.expected, a.err, a.timeout_ns)) return;
+    if (!grid_barrier_g(a.bar, a.expected, a.err, a.timeout_ns, bgen)) return;
     // the winner over all CTAs (identical in every CTA)
     const T* pset = a.pub + (int64_t)(j & 1) * G * slot;
     if (warp == 0) {
