@@ -336,6 +336,8 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
   __shared__ T s_wp[PNW][kPanelNbMax];  // per-warp partials of V^H x (phase B)
   __shared__ T s_dp[kDpCap];  // phase-D chunk sums
   __shared__ T s_wn[kDBatch];                         // D2: updated row-J entries of the batch
+  __shared__ T s_wJ[kDBatch];                         // D2: row-J entries before the update
+  __shared__ T s_fi[kDBatch][kPanelNbMax];            // D2: conj(F) rows of the batch's columns
   __shared__ double s_v1[kDBatch], s_v2[kDBatch];    // D2: squared norms (current, last exact)
   __shared__ int s_need[kDBatch];                     // D2: exact recompute flags
   __shared__ int s_bi;
@@ -461,11 +463,10 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       split_range(J, m, gb, b, u0, u1);
       const int sub = tid & 3;
       constexpr int U = kPanelNbMax / 4;
-      T fp[U], cs[U];
+      T fp[U], cs[U];  // fp: conj(F[p, :]), loaded with the first pass's loads
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int i = sub + 4 * u;
-        fp[u] = (i < kk) ? a.F[(int64_t)p * nb + i] : mk<R>(0, 0);
+        fp[u] = mk<R>(0, 0);
         cs[u] = mk<R>(0, 0);
       }
       double nrm = 0.0;
@@ -486,6 +487,13 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         if (act && sub == 0) {
           cj = colJ[r];
           cp = colP[r];
+        }
+        if (rb == u0) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = sub + 4 * u;
+            if (i < kk) fp[u] = a.F[(int64_t)p * nb + i];
+          }
         }
         if (kk > 0 && act && sub == ((kk - 1) & 3)) {  // previous reflector: rows > J-1, scaled once
           const int u = (kk - 1) >> 2;
@@ -669,6 +677,30 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
     for (int bq = 0; bq < nbat; ++bq) {
       const int cb = c0 + (rev ? nbat - 1 - bq : bq) * nbc;
       const int nc = min(nbc, c1 - cb);
+      // warp 0 stages the D2 epilogue's operands of the batch in shared memory while
+      // the other warps sweep (written before barrier 1 or in earlier steps; F row J
+      // stands in for the pivot column's row)
+      if (warp == 0) {
+        for (int c8 = 0; c8 < nc; c8 += 8) {
+          T fv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int t = cb + c8 + u;
+            fv[u] = (c8 + u < nc && lane < kk) ? a.F[(int64_t)((t == p) ? J : t) * nb + lane] : mk<R>(0, 0);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s_fi[c8 + u][lane] = fv[u];
+        }
+        if (lane < nc) {
+          const int t = cb + lane;
+          const int src = (t == p) ? J : t;
+          s_wJ[lane] = W[J + (int64_t)t * ldw];
+          if (a.pivot) {
+            s_v1[lane] = a.vn1[src];
+            s_v2[lane] = a.vn2[src];
+          }
+        }
+      }
       // D1: chunk sums
       if (a.bulk) {
         // items (column, chunk) dealt round-robin to the sweep warps kNSW..PNW-1
@@ -746,26 +778,6 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
       const T tau = ccast<R>(s_scal[0]), sc = ccast<R>(s_scal[1]);
       const T w_l = lane < kk ? cconj(s_vrow[lane]) + sc * s_wacc[lane] : mk<R>(0, 0);  // V_l^H v
       constexpr int CPW = kDBatch / PNW;  // columns per warp
-      T wJtT[CPW], fiT[CPW];
-      double v1a[CPW], v2a[CPW];
-#pragma unroll
-      for (int q = 0; q < CPW; ++q) {
-        const int cl = warp + PNW * q;
-        wJtT[q] = mk<R>(0, 0);
-        fiT[q] = mk<R>(0, 0);
-        v1a[q] = 0.0;
-        v2a[q] = 0.0;
-        if (cl < nc) {
-          const int t = cb + cl;
-          const int src = (t == p) ? J : t;
-          wJtT[q] = W[J + (int64_t)t * ldw];
-          if (lane < kk) fiT[q] = a.F[(int64_t)src * nb + lane];
-          if (lane == 0 && a.pivot) {
-            v1a[q] = a.vn1[src];
-            v2a[q] = a.vn2[src];
-          }
-        }
-      }
       T fT[CPW];
 #pragma unroll
       for (int q = 0; q < CPW; ++q) {
@@ -784,13 +796,13 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           for (int u = 0; u < 8; ++u)
             if (c8 + u < nchb) acc = acc + dv[u];
         }
-        const T wJt = wJtT[q];
+        const T wJt = s_wJ[cl];
         const T y = cconj(wJt) + sc * acc;
         // F[t, kk] = tau * (y - sum_i F[src, i] w_i); row update of W[J, t]
         // (the array holds conj(F): the trailing update reads it as F^H directly)
         T fw = mk<R>(0, 0), rowu = mk<R>(0, 0);
         if (lane < kk) {
-          const T fi = fiT[q];  // conj(F[src, lane])
+          const T fi = s_fi[cl][lane];  // conj(F[src, lane])
           cfma(fw, cconj(fi), w_l);
           cfma(rowu, s_vrow[lane], fi);
           if (t == p) Ft[lane] = fi;
@@ -806,8 +818,6 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
           Ft[kk] = cconj(f);
           W[J + (int64_t)t * ldw] = wnew;
           s_wn[cl] = wnew;
-          s_v1[cl] = v1a[q];
-          s_v2[cl] = v2a[q];
         }
       }
       // FP64 downdate of the squared norms, one column per lane of warp 0, so that the
@@ -843,7 +853,7 @@ __global__ void __launch_bounds__(PNT, 1) qr_panel_kernel(PanelArgs<T> a) {
         const T* col = W + (int64_t)t * ldw;
         const T* Fs = a.F + (int64_t)src * nb;
         const T f = fT[q];
-        double v1 = 0.0, v2 = v2a[q];
+        double v1 = 0.0, v2 = a.pivot ? s_v2[cl] : 0.0;
         int need = 0;
         if (a.pivot) {
           v1 = s_v1[cl];
@@ -1346,7 +1356,13 @@ static int l2_bytes() {
   });
 }
 
-constexpr int kPanelSmem = 200 * 1024;  // dynamic shared memory of the panel kernel
+constexpr int kPanelSmem = 200 * 1024;  // dynamic shared memory of the sketch-pivot kernel
+// dynamic shared memory of the panel kernel: static + dynamic stays within the 227 KB
+// a CTA may use (its static part holds the D2 staging arrays, twice as large in complex128)
+template <typename T>
+constexpr int panel_smem() {
+  return sizeof(T) == 8 ? 200 * 1024 : 176 * 1024;
+}
 
 constexpr int kCPanelSmem = 200 * 1024;
 
@@ -1389,7 +1405,7 @@ static cudaError_t panel_setup(int& max_blocks) {
   static PerDevice cache;
   cudaError_t err = cudaSuccess;
   const long long r = cache.get([&err]() -> long long {
-    int smem = kPanelSmem;
+    int smem = panel_smem<T>();
     err = cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return -1;
     int per_sm = 0;
@@ -1540,7 +1556,7 @@ static cudaError_t apply_block(const QrPlan<T>& p, int j0, int kbb, const T* Tb,
 template <typename T>
 static cudaError_t launch_panel(PanelArgs<T>& a, unsigned barrier_extra, int gcap, bool cluster_ok, cudaStream_t s) {
   const int m = a.m, j0 = a.j0, kb = a.kb;
-  const int smem = kPanelSmem;
+  const int smem = panel_smem<T>();
   // bulk copies need 16-byte aligned column chunks: an aligned base, a
   // 16-byte multiple column stride and (complex64) chunks of whole row pairs
   a.bulk = (reinterpret_cast<uintptr_t>(a.W) % 16 == 0) && ((a.ldw * (int64_t)sizeof(T)) % 16 == 0) &&
