@@ -986,18 +986,23 @@ struct CPanelArgs {
   c128* Wg;      // this panel's w vectors (column kk = w of step kk)
 };
 
-// Block-wide FP64 sum; the result is returned to every thread of warp 0.
-__device__ __forceinline__ double cp_block_sum(double v, double* s_red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) s_red[warp] = v;
+// Block-wide FP64 sum, the result in thread 0.  The threads' values go through
+// shared memory and four warps (one per scheduler) add 128 each before a warp
+// reduction: four times fewer FP64 warp instructions than a shuffle reduction in
+// every warp, and FP64 instructions are slow on this GPU.
+static_assert(CPT == 512, "cp_block_sum assumes 512 threads");
+__device__ __forceinline__ double cp_block_sum(double v, double* s_part, double* s_red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  s_part[tid] = v;
   __syncthreads();
-  double t = 0.0;
-  if (warp == 0) {
-    t = lane < CPW ? s_red[lane] : 0.0;
-    for (int o = 1; o < CPW; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (warp < 4) {
+    const double* p = s_part + warp * 128 + lane;
+    double t = (p[0] + p[32]) + (p[64] + p[96]);
+    t = warp_sum(t);
+    if (lane == 0) s_red[warp] = t;
   }
-  return t;
+  __syncthreads();
+  return tid == 0 ? (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]) : 0.0;
 }
 
 // Per step J = j0 + kk, with x = column kk below row J:
@@ -1021,6 +1026,7 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
   __shared__ T s_f[kPanelNbMax];          // conj(tau) d_c
   __shared__ T s_d[kPanelNbMax];          // d_c
   __shared__ double s_red[CPW];
+  __shared__ double s_part[CPT];          // cp_block_sum: one value per thread
   __shared__ c128 s_sc[3];                // tau, 1/(alpha-beta), beta
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned cs = gridDim.x;           // CTAs in the cluster (one cluster)
@@ -1044,7 +1050,7 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
         s_j[pr][q] = (J >= r0 && J < r1) ? col[J - r0] : mk<R>(0, 0);
       }
     }
-    const double t = cp_block_sum(part, s_red);
+    const double t = cp_block_sum(part, s_part, s_red);
     if (tid == 0) {
       const bool own = J >= r0 && J < r1;
       const T al = own ? x[J - r0] : mk<R>(0, 0);
@@ -1091,12 +1097,16 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
           sc = mk<double>(0, 0);
           beta = al;
         } else {
+          // two FP64 divisions (1/beta, 1/|alpha - beta|^2) instead of four: on this
+          // GPU every FP64 operation of this single-lane chain is on the step's
+          // critical path
           const double nv = sqrt(al.re * al.re + al.im * al.im + xn);
           const double bt = al.re >= 0.0 ? -nv : nv;
-          tau = mk<double>((bt - al.re) / bt, -al.im / bt);
+          const double ibt = 1.0 / bt;
+          tau = mk<double>((bt - al.re) * ibt, -al.im * ibt);
           const c128 dnm = mk<double>(al.re - bt, al.im);
-          const double dd = dnm.re * dnm.re + dnm.im * dnm.im;
-          sc = mk<double>(dnm.re / dd, -dnm.im / dd);  // 1 / (alpha - beta)
+          const double idd = 1.0 / (dnm.re * dnm.re + dnm.im * dnm.im);
+          sc = mk<double>(dnm.re * idd, -dnm.im * idd);  // 1 / (alpha - beta)
           beta = mk<double>(bt, 0.0);
         }
         s_sc[0] = tau;
