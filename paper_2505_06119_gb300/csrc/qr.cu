@@ -1077,17 +1077,16 @@ __global__ void __launch_bounds__(CPT, 1) qr_cpanel_kernel(CPanelArgs<T> a) {
     cluster_sync();
     if (warp == 0) {
       // reflector, identical in every CTA (partials combined in the same order)
+      // the norm partials of every CTA; alpha from the CTA that owns row J (the
+      // others hold zero), read directly instead of summed
+      const unsigned own = (unsigned)((J - a.j0) / rb);
       double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-      if (lane < (int)cs) {
-        v0 = ld_dsmem_f64(map_cta(&s_r1[par][0], lane));
-        v1 = ld_dsmem_f64(map_cta(&s_r1[par][1], lane));
-        v2 = ld_dsmem_f64(map_cta(&s_r1[par][2], lane));
+      if (lane < (int)cs) v0 = ld_dsmem_f64(map_cta(&s_r1[par][0], lane));
+      if (lane == 0) {
+        v1 = ld_dsmem_f64(map_cta(&s_r1[par][1], own));
+        v2 = ld_dsmem_f64(map_cta(&s_r1[par][2], own));
       }
-      for (int o = 1; o < kClusterMax; o <<= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-      }
+      for (int o = 1; o < kClusterMax; o <<= 1) v0 += __shfl_xor_sync(0xffffffffu, v0, o);
       if (lane == 0) {
         const double xn = v0;
         const c128 al = mk<double>(v1, v2);
