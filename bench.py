@@ -290,10 +290,14 @@ def ours(args):
                                            FLOP_PER_APPLY * chi ** 3 * ws * 1e3 / ms_step64 / 1e12
                                            if ms_step64 else None),
         "fidelity_dev": fid,
-        "roofline": {"bound": "hbm", "kernel": "qr_panel_kernel (pivoted-QR panel: per-step trailing GEMV)",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("qr_panel_kernel (pivoted-QR panel: per-step trailing GEMV)" if args.truncation == "qrcp"
+                                else "panel class of the randomized split (sketch pivots and unpivoted panels: "
+                                     "latency-bound; algorithmic bytes are the sketch's)"),
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / peaks.get("hbm_gbs", 1.0),
-                     "traffic": panel_traffic(panel["alg_bytes"] / max(1, panel["launches"]), chi),
+                     "traffic": (panel_traffic(panel["alg_bytes"] / max(1, panel["launches"]), chi)
+                                 if args.truncation == "qrcp" else None),
                      "traffic_unit": "bytes per launch",
                      "peak_source": peak_src,
                      "launches_timed": panel["launches"], "kernel_ms_per_step": panel["ms"] / args.steps},
