@@ -541,6 +541,10 @@ struct mps_s {
   // layer path (lazy)
   std::vector<Lane> lanes;
   cudaEvent_t ev_fork = nullptr;
+  // look-ahead of the centre moves' QR: a high-priority stream for its critical path
+  // (panels on one cluster) and three events; null when it could not be created
+  cudaStream_t la_stream = nullptr;
+  cudaEvent_t la_ev[3] = {};
   bool graphs = true;           // layers are captured into CUDA graphs after the first call
   long long layer_calls = 0;
   long long graph_launches = 0;  // layers run as a graph launch
@@ -629,6 +633,15 @@ void release(mps_t h) {
   h->graph_cache.clear();
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   h->ev_fork = nullptr;
+  if (h->la_stream) {
+    cudaStreamSynchronize(h->la_stream);
+    cudaStreamDestroy(h->la_stream);
+    h->la_stream = nullptr;
+  }
+  for (cudaEvent_t& e : h->la_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   h->prof.destroy();
   for (void* p : h->allocs) {
     if (h->ufree)
@@ -862,6 +875,21 @@ int tuned_knobs(mps_t h, int i, const T* gt, int chi, const SketchRef* sk, Knobs
 }
 
 // ---- centre moves (Sec. III-C.1): plain QR rightward, LQ leftward, no truncation
+// Look-ahead scratch of a centre move's QR: the main stream's GEMM scratch lives in
+// the Q buffer, which the factorisation does not use (Q is formed after it).
+template <typename T>
+void plan_lookahead(mps_t h, QrPlan<T>& p, const Ws<T>& w) {
+  if (!h->la_stream) return;
+  const int64_t wide = 2 * (int64_t)std::max(h->chicap, 1);
+  const int64_t yz = 2 * (int64_t)p.nb * wide;
+  if (p.n > wide || p.k > wide || 2 * yz + p.sk_cap > h->ldq * (int64_t)std::max(h->chicap, 1)) return;
+  p.s2 = h->la_stream;
+  p.la_ev = h->la_ev;
+  p.Y2 = w.Q;
+  p.Z2 = w.Q + yz;
+  p.SK2 = w.Q + 2 * yz;
+}
+
 template <typename T>
 int move_right(mps_t h, int j) {
   using R = typename real_of<T>::type;
@@ -878,6 +906,7 @@ int move_right(mps_t h, int j) {
   hook_after(hk, MPS_KCLASS_CANON, 1);
   QrPlan<T> p = make_plan<T>(w, h->kn, m, n, k, 0, nullptr, nullptr);
   p.kclass = MPS_KCLASS_CANON;
+  plan_lookahead<T>(h, p, w);
   CUTRY(h, qr_factor<T>(p, s, hk), "move_right qr");
   CUTRY(h, qr_form_q<T>(p, w.Q, w.ldq, s, hk), "move_right form_q");
   hook_before(hk, MPS_KCLASS_CANON, 2.0 * m * k * sizeof(T), 0);
@@ -928,6 +957,7 @@ int move_left(mps_t h, int j) {
   hook_after(hk, MPS_KCLASS_CANON, 1);
   QrPlan<T> p = make_plan<T>(w, h->kn, m, n, k, 0, nullptr, nullptr);
   p.kclass = MPS_KCLASS_CANON;
+  plan_lookahead<T>(h, p, w);
   CUTRY(h, qr_factor<T>(p, s, hk), "move_left qr");
   CUTRY(h, qr_form_q<T>(p, w.Q, w.ldq, s, hk), "move_left form_q");
   // site j (k x 2cr row-major) = Q^H
@@ -1750,6 +1780,24 @@ int mps_create_ex(mps_t* out, int n, int chi_max, const mps_config* cfg_in) {
     h->stream = h->own_stream;
   }
   h->prof.stream = h->stream;
+  {
+    // the centre moves' look-ahead stream, at the highest priority so that the panels
+    // on it get their SMs ahead of the trailing updates; without it the QR runs on
+    // the handle's stream alone
+    int lo = 0, hi = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&h->la_stream, cudaStreamNonBlocking, hi) == cudaSuccess;
+    for (cudaEvent_t& e : h->la_ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      if (h->la_stream) cudaStreamDestroy(h->la_stream);
+      h->la_stream = nullptr;
+      for (cudaEvent_t& e : h->la_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+      }
+    }
+  }
   // bond dims and reserved capacities
   h->bond.assign(n + 1, 1);
   h->capb.resize(n + 1);

@@ -199,6 +199,15 @@ struct QrPlan {
   int* sk_jpvt = nullptr;   // n: column order of the sketch panel
   int* piv_seq = nullptr;   // 2 nb: position taken at each step of a block's pivot choice
   unsigned long long seed = 0;  // generator state of the sketching matrix
+  // pivot == 0 with look-ahead (optional): the panels, their T factors and the
+  // updates of the next outer block run on s2 (a high-priority stream) while the
+  // rest of each trailing update runs on the caller's stream with its own scratch
+  // (Y2, Z2: 2nb * max(n, k); SK2: sk_cap elements); la_ev: three events
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t* la_ev = nullptr;
+  T* Y2 = nullptr;
+  T* Z2 = nullptr;
+  T* SK2 = nullptr;
 };
 
 // randomized QRCP: a block of pivots is two panels (2 nb, at most kSketchBlockMax

@@ -1631,6 +1631,134 @@ static cudaError_t launch_panel(PanelArgs<T>& a, unsigned barrier_extra, int gca
 template <typename T>
 cudaError_t qr_factor_sketched(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks);
 
+// Plain QR (pivot == 0) with look-ahead, for panels that run on one thread-block
+// cluster (16 SMs): while the cluster factors the panels of outer block q + 1, the
+// other SMs apply outer block q's reflector to the columns beyond block q + 1.
+// Per outer block q (panels 2q, 2q + 1), in this order:
+//   s2: panel 2q, its T factor, its update of panel 2q + 1's columns, panel 2q + 1,
+//       its T factor, the outer T factor of the pair;
+//   s2: (after the main stream's update of block q - 1) the pair's reflector on the
+//       columns of block q + 1;
+//   s:  (after the outer factor) the pair's reflector on the columns beyond block q + 1.
+// The two streams use separate GEMM scratch; every column sees the reflectors in
+// order (block q - 1's main-stream update before block q's look-ahead update).
+// Launches are accounted as one bracket on the caller's stream.
+template <typename T>
+static cudaError_t qr_factor_lookahead(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
+  const ClassMap K{p.kclass};
+  const int m = p.m, n = p.n, k = p.k, nb = p.nb;
+  const int npanels = (k + nb - 1) / nb;
+  cudaStream_t s2 = p.s2;
+  cudaEvent_t ev_fork = p.la_ev[0], ev_vt = p.la_ev[1], ev_b = p.la_ev[2];
+  QrPlan<T> pm = p;  // the main stream's scratch
+  pm.Y = p.Y2;
+  pm.Z = p.Z2;
+  pm.SK = p.SK2;
+  int maxb = 1;
+  CK(panel_setup<T>(maxb));
+  const int gcap = std::max(1, std::min(p.G > 0 ? p.G : maxb, maxb));
+  double alg = 0.0;
+  for (int j = 0; j < k; ++j) alg += 8.0 * (m - j) * (std::min(n, (j / nb + 1) * nb) - j);
+  hook_before(hooks, K(MPS_KCLASS_PANEL), 0.0, alg);
+  int nl = 1;
+  CK(cudaMemsetAsync(p.Tfac, 0, sizeof(T) * (size_t)npanels * nb * nb, s));
+  iota_kernel<<<(n + 255) / 256, 256, 0, s>>>(p.jpvt, n);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ev_fork, s));
+  CK(cudaStreamWaitEvent(s2, ev_fork, 0));
+  bool b_issued = false;  // ev_b holds a main-stream update not yet waited for by s2
+  cudaError_t err = cudaSuccess;
+  auto panel = [&](int pi) -> cudaError_t {
+    const int j0 = pi * nb, kb = std::min(nb, k - j0);
+    PanelArgs<T> a;
+    a.W = p.W;
+    a.ldw = p.ldw;
+    a.m = m;
+    a.n = n;
+    a.j0 = j0;
+    a.kb = kb;
+    a.nend = std::min(n, j0 + kb);
+    a.nb = nb;
+    a.pivot = 0;
+    a.F = p.F;
+    a.vn1 = p.vn1;
+    a.vn2 = p.vn2;
+    a.jpvt = p.jpvt;
+    a.tau = p.tau;
+    a.Tp = p.Tfac + (size_t)pi * nb * nb;
+    a.Wg = p.Wg + (size_t)pi * nb * nb;
+    a.red_norm = p.red_norm;
+    a.red_w = reinterpret_cast<T*>(p.red_w);
+    a.red_argv = reinterpret_cast<long long*>(p.red_argv);
+    a.red_argi = p.red_argi;
+    a.alpha_slot = p.alpha_slot;
+    a.bar = p.bar;
+    a.err = p.err;
+    a.timeout_ns = p.timeout_ns;
+    a.flag_tol = p.flag_tol;
+    a.piv_seq = nullptr;
+    CK(launch_panel<T>(a, p.barrier_extra, gcap, true, s2));
+    tfactor_kernel<T><<<1, 1024, 0, s2>>>(p.Wg, p.tau, pi, k, nb, p.Tfac);
+    nl += 2;
+    return cudaGetLastError();
+  };
+  for (int pb = 0; pb < npanels && err == cudaSuccess; pb += 2) {
+    const int jb = pb * nb;
+    const int kb0 = std::min(nb, k - jb);
+    err = panel(pb);
+    if (err != cudaSuccess) break;
+    if (pb + 1 < npanels) {
+      // the first panel's reflector on its partner's columns, then the partner
+      err = apply_block<T>(p, jb, kb0, p.Tfac + (size_t)pb * nb * nb, nb, 1, p.W, p.ldw, jb + kb0,
+                           std::min(nb, k - jb - kb0), &nl, s2);
+      if (err == cudaSuccess) err = panel(pb + 1);
+      if (err != cudaSuccess) break;
+    }
+    int kbb = 0;
+    err = outer_tfactor<T>(p, pb, &kbb, &nl, s2);
+    if (err != cudaSuccess) break;
+    const T* Tb = p.Tblk + (size_t)(pb / 2) * 4 * nb * nb;
+    const int c0 = std::min(k, jb + 2 * nb);         // first column after the pair
+    const int la_end = std::min(n, c0 + 2 * nb);     // end of the next pair's columns
+    if (c0 >= n) continue;
+    if ((err = cudaEventRecord(ev_vt, s2)) != cudaSuccess) break;
+    if (b_issued && (err = cudaStreamWaitEvent(s2, ev_b, 0)) != cudaSuccess) break;
+    b_issued = false;
+    // look-ahead: the next pair's columns, on the critical path
+    err = apply_block<T>(p, jb, kbb, Tb, 2 * nb, 1, p.W, p.ldw, c0, la_end - c0, &nl, s2);
+    if (err != cudaSuccess) break;
+    if (la_end < n) {
+      if ((err = cudaStreamWaitEvent(s, ev_vt, 0)) != cudaSuccess) break;
+      err = apply_block<T>(pm, jb, kbb, Tb, 2 * nb, 1, p.W, p.ldw, la_end, n - la_end, &nl, s);
+      if (err != cudaSuccess) break;
+      if ((err = cudaEventRecord(ev_b, s)) != cudaSuccess) break;
+      b_issued = true;
+    }
+  }
+  // join: the caller's stream continues once the critical-path stream is done
+  cudaError_t e2 = cudaEventRecord(ev_fork, s2);
+  if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev_fork, 0);
+  hook_after(hooks, K(MPS_KCLASS_PANEL), nl);
+  if (err != cudaSuccess) {
+    note_cuda_failure(__FILE__, __LINE__);
+    return err;
+  }
+  CK(e2);
+  return cudaSuccess;
+}
+
+// Whether a plain QR of this plan can run with look-ahead: every panel on the
+// cluster kernel (the first panel, the tallest, fits its shared memory), the
+// caller gave a second stream, and the second scratch set exists.
+template <typename T>
+static bool lookahead_ok(const QrPlan<T>& p) {
+  if (p.pivot != 0 || !p.s2 || !p.la_ev || !p.Y2 || !p.Z2 || !p.SK2 || p.kclass < 0) return false;
+  const int ccs = cpanel_cluster_size<T>();
+  if (ccs <= 0) return false;
+  const int crb = ((p.m + ccs - 1) / ccs + 1) / 2 * 2;
+  return (int64_t)std::min(p.nb, p.k) * crb * (int64_t)sizeof(T) <= kCPanelSmem;
+}
+
 template <typename T>
 cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
   using R = typename real_of<T>::type;
@@ -1652,6 +1780,7 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     return cudaSuccess;
   }
   if (p.pivot == 2) return qr_factor_sketched<T>(p, s, hooks);
+  if (lookahead_ok<T>(p)) return qr_factor_lookahead<T>(p, s, hooks);
   int maxb = 1;
   CK(panel_setup<T>(maxb));
   const int gcap = std::max(1, std::min(p.G > 0 ? p.G : maxb, maxb));
