@@ -1749,7 +1749,8 @@ static cudaError_t qr_factor_lookahead(const QrPlan<T>& p, cudaStream_t s, Launc
 
 // Whether a plain QR of this plan can run with look-ahead: every panel on the
 // cluster kernel (the first panel, the tallest, fits its shared memory), the
-// caller gave a second stream, and the second scratch set exists.
+// caller gave a second stream and the second scratch set, and the plan attributes
+// all its launches to one kernel class (they are timed as one bracket).
 template <typename T>
 static bool lookahead_ok(const QrPlan<T>& p) {
   if (p.pivot != 0 || !p.s2 || !p.la_ev || !p.Y2 || !p.Z2 || !p.SK2 || p.kclass < 0) return false;
