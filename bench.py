@@ -345,7 +345,7 @@ def fidelity_deviation(mm, m64, n, i, args, np):
     out = {"steps": args.fp64_warmup + args.fp64_steps, "f_fp64": f64, "f_mixed": fmx,
            "norm_fidelity_rel": abs(fmx - f64) / f64,
            "scope": "after the listed steps of this workload (a per-step bar); over the 390 truncating gates "
-                    "of the 40-qubit depth-20 brick-wall at chi 1024 the deviation is larger (about 2e-5), "
+                    "of the 40-qubit depth-20 brick-wall at chi 1024 the deviation is larger (about 4e-5 in the norm fidelity), "
                     "set by pivot decisions between residual norms closer than FP32 rounding"}
     if not args.skip_overlap:
         o = mm.overlap(m64)
