@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
     // scalar stores: measured faster there)
     const bool dvec = (BETA || BM == 64) && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && ((ldd & 1) == 0);
     const bool alpha_one = split || (d.alpha.re == 1.f && d.alpha.im == 0.f);
+    float sq[4][2] = {};  // colsq: this thread's rows of each of its columns
 #pragma unroll
     for (int g = 0; g < RG; ++g) {
       const int i = i0 + 32 * g + 2 * tm;
@@ -353,7 +354,27 @@ __global__ void __launch_bounds__(G_NT, BM == 64 ? 2 : 1) gemm_c64_kernel(GemmDe
             cp[0] = v0;
             if (pair) cp[1] = v1;
           }
+          if constexpr (beta_nz) {
+            sq[h][f] += fmaf(v0.re, v0.re, v0.im * v0.im);
+            if (pair) sq[h][f] += fmaf(v1.re, v1.re, v1.im * v1.im);
+          }
         }
+    }
+    if constexpr (beta_nz && BM == 64) {
+      // column sums over the tile's 64 rows: the 16 threads of a column (tm, the
+      // lane's low four bits) combine theirs, the first writes
+      if (d.colsq) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+#pragma unroll
+          for (int f = 0; f < 2; ++f) {
+            float v = sq[h][f];
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            const int j = j0 + 32 * h + 2 * tn + f;
+            if (tm == 0 && j < d.N) d.colsq[(int64_t)blockIdx.x * d.ldcs + j] = v;
+          }
+      }
     }
   }
 }

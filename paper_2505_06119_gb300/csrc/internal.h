@@ -67,6 +67,11 @@ struct GemmDesc {
   // products land in wk (splitk * M * N elements) and are summed in a fixed order.
   int splitk = 0;
   T* wk = nullptr;
+  // complex64, C-reading variant without split-K (optional): per CTA row tile, the
+  // squared norms of the result's columns over the tile's rows, summed in FP32:
+  // colsq[tile * ldcs + j], tile = row / 64
+  float* colsq = nullptr;
+  int64_t ldcs = 0;
 };
 
 // Records where a CUDA call first failed on this host thread (file name and line),

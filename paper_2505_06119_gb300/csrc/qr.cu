@@ -1314,6 +1314,19 @@ __global__ void col_norms_kernel(const T* W, int64_t ldw, int m, int r0, int c0,
   }
 }
 
+// vn1 = vn2 = squared column norms of a trailing block, from the per-tile partial
+// sums (FP32, 64 rows each) that the block's update GEMM produced in its epilogue,
+// added in FP64 in tile order; column j of the block is column c0 + j of W
+__global__ void colsq_reduce_kernel(const float* P, int64_t ldp, int ntile, int N, int c0, double* vn1,
+                                    double* vn2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double s = 0.0;
+  for (int t = 0; t < ntile; ++t) s += (double)P[(int64_t)t * ldp + j];
+  vn1[c0 + j] = s;
+  vn2[c0 + j] = s;
+}
+
 // discarded = sum_{t in [c0, n)} vn1[t] (squared norms), one block, fixed order
 __global__ void discarded_kernel(const double* vn1, int c0, int n, double* out, double* total) {
   __shared__ double s[256];
@@ -1840,6 +1853,11 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
     CK(launch_panel<T>(a, p.barrier_extra, gcap, !p.pivot, s));
     hook_after(hooks, K(MPS_KCLASS_PANEL), 1);
     if (p.pivot) {
+      // complex64: the update's epilogue also sums the squared column norms of the
+      // block it writes (per 64-row tile, into the split-K scratch, which this
+      // update does not use), so the norms need no second pass over the block
+      bool fused = false;
+      int ntile = 0;
       if (J1 < n && J1 < m) {
         GemmDesc<T> d;
         d.M = m - J1;
@@ -1859,12 +1877,26 @@ cudaError_t qr_factor(const QrPlan<T>& p, cudaStream_t s, LaunchHooks* hooks) {
         d.b_mask = MASK_NONE;
         d.C = p.W + J1 + (int64_t)J1 * p.ldw;
         d.ldc = p.ldw;
+        if constexpr (sizeof(T) == 8) {
+          ntile = (d.M + 63) / 64;
+          if (!p.use_tc && gemm_c64_tile_rows(d.M, d.K) == 64 && (int64_t)ntile * d.N <= 2 * p.sk_cap) {
+            d.colsq = reinterpret_cast<float*>(p.SK);
+            d.ldcs = d.N;
+            fused = true;
+          }
+        }
         double M = d.M, N = d.N;
         hook_before(hooks, K(MPS_KCLASS_UPDATE), (2.0 * M * N + (M + N) * kb) * sizeof(T), 8.0 * M * N * kb);
         CK(gemm_auto<T>(d, p.use_tc, p.err, p.timeout_ns, s));
         hook_after(hooks, K(MPS_KCLASS_UPDATE), 1);
       }
-      if (J1 < n) {
+      if (J1 < n && fused) {
+        hook_before(hooks, K(MPS_KCLASS_NORMS), 4.0 * ntile * (n - J1) + 16.0 * (n - J1), (double)ntile * (n - J1));
+        colsq_reduce_kernel<<<(n - J1 + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float*>(p.SK), n - J1, ntile,
+                                                                n - J1, J1, p.vn1, p.vn2);
+        CK(cudaGetLastError());
+        hook_after(hooks, K(MPS_KCLASS_NORMS), 1);
+      } else if (J1 < n) {
         hook_before(hooks, K(MPS_KCLASS_NORMS), (double)std::max(0, m - J1) * (n - J1) * sizeof(T),
                     3.0 * std::max(0, m - J1) * (n - J1));
         int warps = 8;
